@@ -1,0 +1,112 @@
+"""Analytic pins for the oracle (FP64).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+* ``laminate_tangent``: effective stiffness of a grid-aligned laminate (phase
+  depends on the x index only).  The exact displacement is piecewise linear
+  in x with kinks on grid planes, which linear elements represent exactly
+  (Sec. 2.6), so the discrete solution must reproduce this closed form.
+* ``voigt_reuss``: the arithmetic and harmonic means of the element
+  stiffnesses, which bound any effective stiffness that minimises the
+  elastic energy (Eq. stat-mech-equi2 is its stationarity condition).
+* ``textbook_strain_projection``: the small-strain projection of Appendix B
+  evaluated with the Fourier derivative ik and one evaluation point, in the
+  classical closed form in n = k/|k| (Appendix B points to Milton 1988).
+* ``appendix_b_projection``: the index form of Appendix B written out
+  literally with (potentially discrete) element derivatives D_Theta(k):
+  D^-1 = D*/(sum_L D_L . D_L*), g_TL = D_T (x) D_L^-1,
+  h = (1 + sum_T g_TT)^-1, and
+  G_TL,ijlm = (g_TL,il h_jm + g_TL,im h_jl + g_TL,jl h_im + g_TL,jm h_il)/2.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .fe_projection import lame, mandel_pairs, n_strain, stiffness_mandel
+
+
+def laminate_tangent(layer_E, nu, dim):
+    """Closed-form Mandel C_eff of layers normal to x with moduli ``layer_E`` (equal thickness).
+
+    Continuity across the layers keeps the in-plane strains and the traction
+    (sigma_xx, sigma_xy, sigma_xz) uniform; averaging gives, with M = lambda + 2 mu:
+    C_xxxx = <1/M>^-1, C_xxyy = <lambda/M><1/M>^-1,
+    C_yyyy = <M - lambda^2/M> + <lambda/M>^2 <1/M>^-1,
+    C_yyzz = <lambda - lambda^2/M> + <lambda/M>^2 <1/M>^-1,
+    x-shears (Mandel) 2 <1/mu>^-1, the in-layer shear 2 <mu>.
+    """
+    lam, mu = lame(np.asarray(layer_E, dtype=np.float64), nu)
+    M = lam + 2.0 * mu
+    iM = np.mean(1.0 / M)
+    lM = np.mean(lam / M)
+    ns = n_strain(dim)
+    C = np.zeros((ns, ns))
+    C[0, 0] = 1.0 / iM
+    for t in range(1, dim):
+        C[0, t] = C[t, 0] = lM / iM
+    for s in range(1, dim):
+        for t in range(1, dim):
+            if s == t:
+                C[s, t] = np.mean(M - lam ** 2 / M) + lM ** 2 / iM
+            else:
+                C[s, t] = np.mean(lam - lam ** 2 / M) + lM ** 2 / iM
+    pairs = mandel_pairs(dim)
+    for s in range(dim, ns):
+        i, j = pairs[s]
+        if i == 0 or j == 0:
+            C[s, s] = 2.0 / np.mean(1.0 / mu)
+        else:
+            C[s, s] = 2.0 * np.mean(mu)
+    return C
+
+
+def voigt_reuss(E_field, nu, dim):
+    """(Voigt, Reuss) Mandel bounds of a per-voxel isotropic field."""
+    Cbar = stiffness_mandel(dim, 1.0, nu)
+    Ev = np.asarray(E_field).reshape(-1)
+    voigt = Cbar * np.mean(Ev)
+    reuss = np.linalg.inv(np.linalg.inv(Cbar) * np.mean(1.0 / Ev))
+    return voigt, reuss
+
+
+def textbook_strain_projection(kvec):
+    """Classical small-strain compatibility projection for one wavevector, k != 0.
+
+    G_ijlm = (n_i n_l d_jm + n_i n_m d_jl + n_j n_l d_im + n_j n_m d_il)/2 - n_i n_j n_l n_m,
+    n = k/|k|.  Returned as a full (D, D, D, D) real tensor.
+    """
+    k = np.asarray(kvec, dtype=np.float64)
+    nvec = k / np.linalg.norm(k)
+    D = len(k)
+    d = np.eye(D)
+    G = np.zeros((D, D, D, D))
+    for i in range(D):
+        for j in range(D):
+            for l in range(D):
+                for m in range(D):
+                    G[i, j, l, m] = 0.5 * (nvec[i] * nvec[l] * d[j, m] + nvec[i] * nvec[m] * d[j, l]
+                                           + nvec[j] * nvec[l] * d[i, m] + nvec[j] * nvec[m] * d[i, l]) \
+                        - nvec[i] * nvec[j] * nvec[l] * nvec[m]
+    return G
+
+
+def appendix_b_projection(Dsym):
+    """Literal Appendix-B small-strain projection for one wavevector.
+
+    ``Dsym``: (n_q, D) complex element derivatives D_Theta(k), not all zero.
+    Returns G[T, i, j, L, l, m] with projected strain
+    e'_T,ij = sum_L,l,m G[T, i, j, L, l, m] e_L,ml.
+    """
+    Dsym = np.asarray(Dsym, dtype=np.complex128)
+    nq, D = Dsym.shape
+    S = np.sum(Dsym * np.conj(Dsym)).real
+    Dinv = np.conj(Dsym) / S
+    g = np.einsum("ti,lj->tlij", Dsym, Dinv)          # g_TL,ij = D_T,i D^-1_L,j
+    h = np.linalg.inv(np.eye(D) + sum(g[t, t] for t in range(nq)))
+    G = np.zeros((nq, D, D, nq, D, D), dtype=np.complex128)
+    for t in range(nq):
+        for L in range(nq):
+            gt = g[t, L]
+            G[t, :, :, L, :, :] = 0.5 * (np.einsum("il,jm->ijlm", gt, h) + np.einsum("im,jl->ijlm", gt, h)
+                                         + np.einsum("jl,im->ijlm", gt, h) + np.einsum("jm,il->ijlm", gt, h))
+    return G
