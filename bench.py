@@ -1,0 +1,336 @@
+"""Throughput of the projected-CG homogenization solver on one GB300 (or N replicas).
+
+A step is one converged effective-tangent solve of one RVE: all load cases
+(the unit Mandel strains) to the accuracy target, then the homogenised
+effective stiffness.  Default workload: 2D 1024x1024 two-phase thresholded
+Gaussian field, contrast 100, nu = 0.3, 3 load cases, FP32-FFT inner solve
+with FP64 refinement.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per projected-CG iteration and solves/s at 1e-9 rel. err; % HBM roofline"
+
+WORKLOADS = {
+    # name: (microstructures config, precision, relative residual tolerance)
+    "gauss1024": ("gauss1024", "mixed", 1e-11),
+    "gauss1024_fp64": ("gauss1024", "fp64", 1e-11),
+    "lognormal64": ("lognormal64", "mixed", 1e-11),
+    "spheres128": ("spheres128", "mixed", 1e-11),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def model_bytes(dim, n, s, L_iters):
+    """Algorithmic bytes of the CG-iteration passes, per load-case iteration.
+
+    s: bytes per real scalar of the inner precision.  Returns dict pass -> bytes.
+    Pass A reads r, p_old and E and writes p and the x-spectrum; pass C (2D)
+    reads and writes the spectrum once; pass E reads the spectrum and x, r, p
+    and writes x and r.  In 3D passes B, C, D each read and write the spectrum.
+    """
+    nq, ns = (2, 3) if dim == 2 else (6, 6)
+    m = nq * ns
+    N = int(np.prod(n))
+    kx = n[0] // 2 + 1
+    spec = m * kx * (N // n[0]) * 2 * s
+    out = {
+        "pass_a": 3 * m * N * s + N * s + spec,
+        "pass_c": 2 * spec,
+        "pass_e": spec + 5 * m * N * s,
+    }
+    if dim == 3:
+        out["pass_b"] = 2 * spec
+        out["pass_d"] = 2 * spec
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(cfg_name, seconds_budget=20.0):
+    """Time the FP64 oracle's CG iterations on this host (bounded sample).
+
+    Returns (seconds per CG iteration per load case, iterations timed, cores).
+    """
+    import microstructures as ms
+    from oracle.fe_projection import Problem
+    cfg = ms.config_inputs(cfg_name)
+    P = Problem(cfg["n"], cfg["E"], cfg["nu"])
+    Ef = P.broadcast_macro(cfg["E_macro"][0])
+    r = -P.operator(Ef)
+    p = r.copy()
+    x = np.zeros_like(r)
+    rr = float(np.sum(r * r))
+    its = 0
+    t0 = time.perf_counter()
+    while True:
+        q = P.operator(p)
+        alpha = rr / float(np.sum(p * q))
+        x += alpha * p
+        r -= alpha * q
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        its += 1
+        if time.perf_counter() - t0 > seconds_budget and its >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return dt / its, its, 1
+
+
+def golden_iterations(cfg_name):
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", cfg_name + ".json")) as f:
+            d = json.load(f)
+        return d.get("iterations"), d.get("C_eff")
+    except Exception:
+        return None, None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg_name, prec, tol = WORKLOADS[args.workload]
+    its_gold, _ = golden_iterations(cfg_name)
+    total_its = sum(its_gold) if its_gold else None
+    per_step = []
+    sample_its = 0
+    budget = max(3.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for k in range(args.warmup + args.steps):
+        sec_it, its, cores = oracle_sample(cfg_name, seconds_budget=budget)
+        if k >= args.warmup:
+            per_step.append(sec_it)
+            sample_its += its
+    sec_it = float(np.mean(per_step))
+    ms_it = sec_it * 1e3
+    solve_s = sec_it * total_its if total_its else None
+    value = (1.0 / solve_s) if solve_s else None
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3 if solve_s else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg_name},
+        "ms_per_cg_iteration": ms_it,
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample_its} FP64 CG iterations of one load case of {cfg_name} "
+                                   f"(numpy oracle), scaled by the {total_its} iterations of the full solve"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2105_03297_gb300.build import build_library
+    if rank == 0 or world == 1:
+        build_library()
+    if world > 1:
+        dist.barrier()
+    import microstructures as ms
+    from paper_2105_03297_gb300 import RVE
+
+    cfg_name, prec, tol = WORKLOADS[args.workload]
+    cfg = ms.config_inputs(cfg_name)
+    n, E, nu, Em = cfg["n"], cfg["E"], cfg["nu"], cfg["E_macro"]
+    dim = len(n)
+    L = len(Em)
+    stream = torch.cuda.current_stream()
+    r = RVE(n, precision=prec, stream=stream.cuda_stream)
+    E_dev = torch.from_numpy(E.reshape(-1)).cuda()
+    r.set_material(E_dev, nu)
+    max_iter = 20000
+    for _ in range(args.warmup):
+        code, info = r.solve(Em, rel_tol=tol, max_iter=max_iter)
+        C = r.effective_tangent()
+    _, C_gold = golden_iterations(cfg_name)
+    acc = float(np.abs(C - np.array(C_gold)).max() / np.abs(np.array(C_gold)).max()) if C_gold else None
+    r.timing(True)
+    r.timing_read()
+    iters = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            code, info = r.solve(Em, rel_tol=tol, max_iter=max_iter)
+            C = r.effective_tangent()
+            iters.append([i["iterations"] for i in info])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    kt = r.timing_read()
+    r.timing(False)
+    ms_step = ms_total / args.steps
+    lc_iters = float(np.sum(iters)) / args.steps          # load-case iterations per solve
+    cg_iters = float(np.mean([max(v) for v in iters]))   # batched iterations per solve
+    s = 4 if prec == "mixed" else 8
+    mb = model_bytes(dim, n, s, lc_iters)
+    # dominant kernel: the CG-iteration pass with the most device time
+    cand = {k: v for k, v in kt.items() if k in mb and v[1] > 0}
+    dom = max(cand, key=lambda k: cand[k][0])
+    dom_ms, dom_launches = cand[dom]
+    bytes_total = mb[dom] * lc_iters * args.steps
+    achieved = bytes_total / (dom_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    cg_ms = sum(v[0] for k, v in kt.items() if k in mb) / (cg_iters * args.steps)
+
+    # end to end through the C ABI with host buffers: E host->device, C_eff device->host
+    E_host = np.ascontiguousarray(E.reshape(-1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.set_material(E_host, nu)
+        r.solve(Em, rel_tol=tol, max_iter=max_iter)
+        C_h = r.effective_tangent()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    value = world * 1000.0 / ms_step
+    launches = int(sum(v[1] for v in kt.values()))
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": cfg_name, "grid": list(n), "load_cases": L, "precision": prec,
+                   "rel_tol": tol, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (working set > 129 MB)"},
+        "ms_per_cg_iteration": cg_ms,
+        "cg_iterations_per_solve": cg_iters,
+        "c_eff_rel_err_vs_oracle": acc,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": dom,
+                     "peak_source": peak_kind},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(E_host.nbytes + Em.nbytes),
+                "d2h_bytes_per_step": int(C_h.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        its_gold, _ = golden_iterations(cfg_name)
+        total_its = sum(its_gold) if its_gold else lc_iters
+        sec_it, its, cores = oracle_sample(cfg_name, seconds_budget=15.0)
+        v = 1.0 / (sec_it * total_its)
+        out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{its} FP64 CG iterations of one load case (numpy oracle, "
+                                         f"{sec_it * 1e3:.0f} ms each), scaled by {total_its} iterations per solve"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="gauss1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * rve.h -- C ABI of the GB300 linear-finite-element compatibility-projection
+ * homogenization solver (Leute et al., "Elimination of ringing artifacts by
+ * finite-element projection in FFT-based homogenization").
+ *
+ * Problem (Sec. 2.1, Eqs. stat-mech-equi2 and stat-mech-equi-FFT-homogenization;
+ * small-strain form of Appendix B): a periodic cell of n_x * n_y (* n_z)
+ * voxels, each split into linear finite elements (Sec. 2.6: two triangles per
+ * pixel in 2D; six Kuhn tetrahedra per voxel in 3D), isotropic small-strain
+ * elasticity with a per-voxel Young's modulus and one Poisson ratio (plane
+ * strain in 2D).  For a macroscopic strain E the solver finds the compatible,
+ * mean-free strain fluctuation eps~ with  G * C : (E + eps~) = 0, where
+ * G(k) = B(k) (B(k)^H B(k))^-1 B(k)^H is the projection onto compatible
+ * fields built from the Fourier symbols of the element gradient stencils
+ * (Eqs. genfourderiv, discrete_projection_op, small-strain-eq2), with
+ * G(0) = 0 so that every element keeps the macroscopic strain as its mean
+ * (the k = 0 rule of Sec. 2.3).  The solver is a projected conjugate
+ * gradient (the gradient-based optimiser of Sec. 2.1).
+ *
+ * Conventions
+ *  - Grid sizes n[0] = n_x, n[1] = n_y (, n[2] = n_z).  Supported: powers of
+ *    two, 16..1024 per axis in 2D and 16..256 per axis in 3D.  Other sizes
+ *    return RVE_ERR_UNSUPPORTED_SIZE (there is no CPU fallback).
+ *  - Per-voxel arrays: x fastest, index v = x + n_x*(y + n_y*z).
+ *  - Strain/stress vectors use Mandel notation: 2D (xx, yy, sqrt2*xy),
+ *    3D (xx, yy, zz, sqrt2*yz, sqrt2*xz, sqrt2*xy); n_s = 3 or 6.
+ *  - A strain FIELD holds m = n_q*n_s scalars per voxel, component-major:
+ *    array [m][N] with component c = Theta*n_s + s (element Theta, Mandel s).
+ *    Element order: 2D Theta=0 on nodes {00,10,01}, Theta=1 on {11,01,10};
+ *    3D Theta = lexicographic index of the permutation (a,b,c) of (x,y,z),
+ *    tetrahedron {0, e_a, e_a+e_b, e_a+e_b+e_c}.
+ *  - Nodal fields (displacements) hold D scalars per node, [D][N]; node v is
+ *    the lower corner of voxel v.
+ *  - DFT convention of Appendix A (forward exp(-i k.r), inverse with 1/N).
+ *
+ * Memory and streams
+ *  - A handle owns all of its device memory; caller buffers are borrowed for
+ *    the duration of a call only.  Pointers flagged RVE_PTR_DEVICE are device
+ *    pointers on the handle's device, otherwise host pointers.
+ *  - All work is enqueued on the CUDA stream given to rve_create (0 = the
+ *    legacy default stream).  Calls returning results to host memory
+ *    synchronise that stream before returning.  A handle must not be used by
+ *    two host threads at once.
+ *
+ * Errors: every function returns RVE_OK (0) or a negative code; the text of a
+ * code is rve_error_string(code).  After RVE_ERR_CUDA the handle should be
+ * destroyed.  RVE_ERR_NOT_CONVERGED leaves readable (unconverged) results.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rve_s* rve_t;
+
+enum {
+  RVE_OK = 0,
+  RVE_ERR_ARG = -1,              /* invalid argument or call order */
+  RVE_ERR_UNSUPPORTED_SIZE = -2, /* grid size outside the GPU FFT's range */
+  RVE_ERR_CUDA = -3,             /* a CUDA runtime call failed */
+  RVE_ERR_OOM = -4,              /* device allocation failed */
+  RVE_ERR_NOT_CONVERGED = -5,    /* max_iter reached before the tolerance */
+  RVE_ERR_NONFINITE = -6,        /* NaN/Inf or CG breakdown (non-positive curvature) */
+  RVE_ERR_TIMEOUT = -7           /* a device-side wait exceeded its limit */
+};
+
+enum { RVE_FP64 = 0, RVE_MIXED = 1 };          /* precision of rve_create */
+enum { RVE_F32 = 0, RVE_F64 = 1 };              /* dtype codes */
+enum { RVE_PTR_HOST = 0, RVE_PTR_DEVICE = 1 };  /* pointer flags */
+
+typedef struct {
+  int32_t iterations;     /* projected-CG iterations (summed over refinement steps) */
+  int32_t refine_steps;   /* outer FP64 refinement steps (1 for RVE_FP64) */
+  int32_t status;         /* RVE_OK or RVE_ERR_NOT_CONVERGED / RVE_ERR_NONFINITE */
+  int32_t reserved;
+  double rel_residual;    /* final ||f|| / ||f_0|| of the FP64 nodal residual f = B^T C (E + eps~) */
+  double cg_rel_residual; /* final relative residual of the last projected-CG solve */
+} rve_info;
+
+/* Text of a status code (static storage). */
+const char* rve_error_string(int code);
+
+/* Create a solver for a dim-dimensional periodic grid.
+ *  n[dim]      voxels per axis (x first);
+ *  length[dim] cell edge lengths (NULL = unit cell); voxel size = length/n (Appendix A);
+ *  precision   RVE_FP64: every step in FP64.  RVE_MIXED: FFTs, projection and
+ *              material in FP32 inside an FP64 iterative refinement on the nodal
+ *              displacement (CG scalars and reductions in FP64);
+ *  cuda_stream a cudaStream_t (NULL = default stream).
+ * Allocates device memory for one load case; more is allocated by rve_solve. */
+int rve_create(rve_t* out, int dim, const int64_t* n, const double* length,
+               int precision, void* cuda_stream);
+
+/* Destroy a handle and free its device memory.  NULL is accepted. */
+int rve_destroy(rve_t h);
+
+/* Set the material: per-voxel Young's modulus E[N] (dtype RVE_F32/RVE_F64,
+ * must be finite and > 0) and the Poisson ratio nu in (-1, 0.5)
+ * (isotropic small-strain Hooke's law, Sec. 3.3; plane strain in 2D). */
+int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_flags);
+
+/* Solve L load cases together.  E_macro[L][n_s] (host, Mandel) are the
+ * macroscopic strains (the k = 0 mode, Sec. 2.3).  rel_tol bounds the final
+ * relative FP64 nodal residual ||B^T C (E + eps~)|| / ||B^T C E||; max_iter
+ * bounds the projected-CG iterations of each load case.  info[L] (host,
+ * may be NULL) receives per-load-case statistics.  Returns the worst status. */
+int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_iter,
+              rve_info* info);
+
+/* Mean stresses of the solved load cases: S[L][n_s] (host, FP64), the volume
+ * average of C : (E_l + eps~_l) over all elements. */
+int rve_mean_stress(rve_t h, double* S);
+
+/* Effective tangent C_eff[n_s][n_s] (host, FP64, Mandel, row-major) from the
+ * last solve, which must have had L = n_s linearly independent load cases:
+ * the matrix with C_eff E_macro[l] = S[l] for every l, i.e.
+ * C_eff = S^T M^-T with M[l][:] = E_macro[l]. */
+int rve_effective_tangent(rve_t h, double* C);
+
+/* Adjoint gradient of J = sum_ab W[a][b] C_eff[a][b] with respect to the
+ * per-voxel Young's moduli, grad_E[N] (FP64).  Needs a preceding solve with
+ * L = n_s independent load cases.  For every row a of W that is not zero it
+ * runs the adjoint projected-CG solve (same operator, right-hand side -G C e_a)
+ * and then forms
+ *   dJ/dE_v = 1/(N n_q) sum_{Theta in v} sum_{a,l} W'[a][l]
+ *             (e_a + lambda_a)_Theta : Cbar : eps_l,Theta,    W' = W M^-1. */
+int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter,
+                void* grad_E, int ptr_flags);
+
+/* Total strain field of a solved load case, eps[m][N] in FP64 (E + eps~). */
+int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags);
+
+/* One application of the projected operator q = G * (C : p) to a field
+ * p[m][N] (dtype of the handle's inner precision: RVE_F64 for RVE_FP64,
+ * RVE_F32 for RVE_MIXED), written to q[m][N].  With apply_material = 0 the
+ * material step is skipped and q = G * p (the bare projection). */
+int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int ptr_flags);
+
+/* Measurement hooks (not part of the method).  With timing enabled, every
+ * kernel launch of the solver is bracketed by CUDA events on the handle's
+ * stream; rve_timing_read returns, per kernel kind, the summed device time in
+ * milliseconds and the number of launches since the last read, and resets
+ * them.  Kinds (index), counting launches inside projected-CG iterations:
+ * 0 pass A (material + x FFT), 1 pass B (y FFT, 3D), 2 pass C (last-axis FFT
+ * + projection), 3 pass D (inverse y FFT, 3D), 4 pass E (inverse x FFT + CG
+ * update); 5 the FP64 residual; 6 every other launch (right-hand side,
+ * displacement recovery, homogenisation). */
+#define RVE_NKINDS 7
+int rve_timing_enable(rve_t h, int enable);
+int rve_timing_read(rve_t h, double* ms /*[RVE_NKINDS]*/, int64_t* launches /*[RVE_NKINDS]*/);
+
+/* Number of voxels N and strain scalars per voxel m of a handle. */
+int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

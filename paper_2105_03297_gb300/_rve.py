@@ -1,0 +1,213 @@
+"""ctypes binding of ``librve.so`` (the C ABI declared in include/rve.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Loading fails loudly when the library is missing; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librve.so")
+
+RVE_OK = 0
+RVE_ERR_ARG = -1
+RVE_ERR_UNSUPPORTED_SIZE = -2
+RVE_ERR_CUDA = -3
+RVE_ERR_OOM = -4
+RVE_ERR_NOT_CONVERGED = -5
+RVE_ERR_NONFINITE = -6
+RVE_ERR_TIMEOUT = -7
+RVE_FP64, RVE_MIXED = 0, 1
+RVE_F32, RVE_F64 = 0, 1
+RVE_PTR_HOST, RVE_PTR_DEVICE = 0, 1
+
+
+class rve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("refine_steps", C.c_int32), ("status", C.c_int32),
+                ("reserved", C.c_int32), ("rel_residual", C.c_double), ("cg_rel_residual", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+# name -> (restype, argtypes), one entry per function of include/rve.h
+SIGNATURES = {
+    "rve_error_string": (C.c_char_p, [C.c_int]),
+    "rve_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                             C.c_int, C.c_void_p]),
+    "rve_destroy": (C.c_int, [C.c_void_p]),
+    "rve_set_material": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int]),
+    "rve_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int,
+                            C.POINTER(rve_info)]),
+    "rve_mean_stress": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "rve_effective_tangent": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "rve_adjoint": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int, C.c_void_p, C.c_int]),
+    "rve_get_strain": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "rve_timing_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "rve_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                            C.POINTER(C.c_int)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librve.so and declare its prototypes (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class RveError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().rve_error_string(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def _check(code, where, allow=()):
+    if code != RVE_OK and code not in allow:
+        raise RveError(code, where)
+    return code
+
+
+def _dptr(arr):
+    """(pointer, flag, keepalive) of a numpy array or a CUDA torch tensor."""
+    if isinstance(arr, np.ndarray):
+        return arr.ctypes.data_as(C.c_void_p), RVE_PTR_HOST, arr
+    import torch
+    if isinstance(arr, torch.Tensor):
+        if not arr.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        flag = RVE_PTR_DEVICE if arr.is_cuda else RVE_PTR_HOST
+        return C.c_void_p(arr.data_ptr()), flag, arr
+    raise TypeError(type(arr))
+
+
+class RVE:
+    """A periodic RVE solver handle (one grid, one precision)."""
+
+    def __init__(self, n, precision="fp64", length=None, stream=None):
+        lib = load()
+        self.n = tuple(int(v) for v in n)
+        self.dim = len(self.n)
+        self.precision = precision
+        nn = (C.c_int64 * self.dim)(*self.n)
+        ln = (C.c_double * self.dim)(*length) if length is not None else None
+        h = C.c_void_p()
+        prec = RVE_MIXED if precision == "mixed" else RVE_FP64
+        st = C.c_void_p(stream) if stream is not None else None
+        _check(lib.rve_create(C.byref(h), self.dim, nn, ln, prec, st), "rve_create")
+        self.h = h
+        N = C.c_int64(); m = C.c_int(); ns = C.c_int(); d = C.c_int()
+        _check(lib.rve_sizes(h, C.byref(N), C.byref(m), C.byref(ns), C.byref(d)), "rve_sizes")
+        self.N, self.m, self.ns = N.value, m.value, ns.value
+        self.inner_dtype = np.float32 if precision == "mixed" else np.float64
+        self.L = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_material(self, E, nu):
+        if isinstance(E, np.ndarray):
+            E = np.ascontiguousarray(E)
+            dt = RVE_F32 if E.dtype == np.float32 else RVE_F64
+            if E.dtype not in (np.float32, np.float64):
+                E = E.astype(np.float64); dt = RVE_F64
+        else:
+            import torch
+            dt = RVE_F32 if E.dtype == torch.float32 else RVE_F64
+        assert int(np.prod(E.shape)) == self.N
+        p, flag, _keep = _dptr(E)
+        _check(load().rve_set_material(self.h, p, dt, float(nu), flag), "rve_set_material")
+
+    def solve(self, E_macro, rel_tol=1e-10, max_iter=5000):
+        Em = np.ascontiguousarray(np.atleast_2d(np.asarray(E_macro, dtype=np.float64)))
+        assert Em.shape[1] == self.ns
+        L = Em.shape[0]
+        info = (rve_info * L)()
+        code = load().rve_solve(self.h, Em.ctypes.data_as(C.POINTER(C.c_double)), L, float(rel_tol),
+                                int(max_iter), info)
+        _check(code, "rve_solve", allow=(RVE_ERR_NOT_CONVERGED,))
+        self.L = L
+        return code, [i.as_dict() for i in info]
+
+    def mean_stress(self):
+        S = np.zeros((self.L, self.ns))
+        _check(load().rve_mean_stress(self.h, S.ctypes.data_as(C.POINTER(C.c_double))), "rve_mean_stress")
+        return S
+
+    def effective_tangent(self):
+        Cm = np.zeros((self.ns, self.ns))
+        _check(load().rve_effective_tangent(self.h, Cm.ctypes.data_as(C.POINTER(C.c_double))),
+               "rve_effective_tangent")
+        return Cm
+
+    def adjoint(self, W, rel_tol=1e-10, max_iter=5000, out=None):
+        W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+        if out is None:
+            out = np.zeros(self.N)
+        p, flag, _keep = _dptr(out)
+        code = load().rve_adjoint(self.h, W.ctypes.data_as(C.POINTER(C.c_double)), float(rel_tol),
+                                  int(max_iter), p, flag)
+        _check(code, "rve_adjoint", allow=(RVE_ERR_NOT_CONVERGED,))
+        return out
+
+    def get_strain(self, load_case, out=None):
+        if out is None:
+            out = np.zeros((self.m, self.N))
+        p, flag, _keep = _dptr(out)
+        _check(load().rve_get_strain(self.h, int(load_case), p, flag), "rve_get_strain")
+        return out
+
+    KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other")
+
+    def timing(self, enable):
+        _check(load().rve_timing_enable(self.h, 1 if enable else 0), "rve_timing_enable")
+
+    def timing_read(self):
+        ms = (C.c_double * 7)()
+        cnt = (C.c_int64 * 7)()
+        _check(load().rve_timing_read(self.h, ms, cnt), "rve_timing_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KINDS)}
+
+    def apply_operator(self, p, material=True, out=None):
+        if isinstance(p, np.ndarray):
+            p = np.ascontiguousarray(p, dtype=self.inner_dtype)
+            if out is None:
+                out = np.zeros_like(p)
+        pp, flag, _k1 = _dptr(p)
+        qp, flag2, _k2 = _dptr(out)
+        assert flag == flag2
+        _check(load().rve_apply_operator(self.h, pp, qp, 1 if material else 0, flag), "rve_apply_operator")
+        return out

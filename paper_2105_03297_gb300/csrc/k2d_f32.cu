@@ -1,0 +1,7 @@
+// 2D pass kernels, FP32 instances (inner solve of the mixed-precision path).
+#include "pass2d.cuh"
+namespace rve {
+template cudaError_t launch_pass_a_2d<float>(const PassArgs<float>&, cudaStream_t);
+template cudaError_t launch_pass_c_2d<float>(const PassArgs<float>&, cudaStream_t);
+template cudaError_t launch_pass_e_2d<float>(const PassArgs<float>&, cudaStream_t);
+}  // namespace rve

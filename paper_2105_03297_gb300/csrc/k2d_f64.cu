@@ -1,0 +1,7 @@
+// 2D pass kernels, FP64 instances.
+#include "pass2d.cuh"
+namespace rve {
+template cudaError_t launch_pass_a_2d<double>(const PassArgs<double>&, cudaStream_t);
+template cudaError_t launch_pass_c_2d<double>(const PassArgs<double>&, cudaStream_t);
+template cudaError_t launch_pass_e_2d<double>(const PassArgs<double>&, cudaStream_t);
+}  // namespace rve

@@ -1,0 +1,715 @@
+// C ABI of the projected-CG homogenization solver: handle lifetime, device
+// memory, host-side tables, and the solve driver.
+//
+// Solve structure (both precisions):
+//   state: FP64 nodal fluctuation displacement u (D per node), so that the
+//   strain E + B u is compatible by construction;
+//   outer step: FP64 real-space residual f = B^T C (E + B u) (no FFT);
+//     inner right-hand side r0 = -G C (E + B u) = -F^-1[B (B^H B)^-1 F[f]];
+//     projected CG on the strain correction delta (Sec. 2.1; iterates stay
+//     compatible because every search direction lies in the range of G);
+//     delta -> u update through u^ = (B^H B)^-1 B^H delta^  (accumulated in FP64).
+//   RVE_FP64 runs the inner solve in FP64 (normally one outer step);
+//   RVE_MIXED runs it in FP32 and refines until the FP64 residual meets the
+//   tolerance.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rve.h"
+#include "rve_internal.h"
+
+using namespace rve;
+
+struct rve_s {
+  int dim = 0, n[3] = {1, 1, 1};
+  int64_t N = 0;
+  double len[3] = {1, 1, 1};
+  int precision = RVE_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int ns = 0, nq = 0, m = 0, D = 0, kx = 0;
+  double nu = 0.0, lam = 0.0, mu2 = 0.0;
+  bool has_material = false;
+  size_t tsize = 8;  // bytes of the inner precision
+  // device memory
+  double* E64 = nullptr;
+  void* Ein = nullptr;  // E in the inner precision (aliases E64 for FP64)
+  void* x = nullptr; void* r = nullptr; void* p = nullptr;
+  void* fbuf = nullptr;
+  void* spec = nullptr; void* spec2 = nullptr;
+  double* u = nullptr;
+  double* uadj = nullptr;
+  double* part = nullptr;
+  int part_stride = 0;
+  CgState* cg = nullptr;
+  CgState* cg_h = nullptr;  // pinned
+  double* emac_d = nullptr;
+  double* emac_adj_d = nullptr;
+  double* hpart = nullptr;
+  int hpart_cap = 0;
+  void* ph[3] = {nullptr, nullptr, nullptr};
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  int Lcap = 0;
+  // results of the last solve
+  int L_solved = 0;
+  bool solved = false;
+  std::vector<double> emac_h;  // [L][ns]
+  std::vector<double> S_h;     // [L][ns]
+  // kernel timing (measurement hook)
+  bool timing = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  double t_ms[RVE_NKINDS] = {0};
+  int64_t t_cnt[RVE_NKINDS] = {0};
+};
+
+namespace {
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return map_err(e_);    \
+  } while (0)
+
+int map_err(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return RVE_ERR_OOM; }
+  return RVE_ERR_CUDA;
+}
+
+enum { K_A = 0, K_B = 1, K_C = 2, K_D = 3, K_E = 4, K_RES = 5, K_OTHER = 6 };
+
+// Launch fn() on the handle's stream; with timing on, bracket it with events.
+template <typename F> cudaError_t timed(rve_s* h, int kind, F fn) {
+  if (!h->timing) return fn();
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (!h->ev_pool.empty()) { ev = h->ev_pool.back(); h->ev_pool.pop_back(); }
+  else {
+    cudaEventCreate(&ev.first);
+    cudaEventCreate(&ev.second);
+  }
+  cudaEventRecord(ev.first, h->stream);
+  cudaError_t e = fn();
+  cudaEventRecord(ev.second, h->stream);
+  h->pending.push_back({kind, ev.first, ev.second});
+  return e;
+}
+
+// Accumulate the elapsed times of completed launches (stream synchronised).
+void flush_timing(rve_s* h) {
+  for (auto& r : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      h->t_ms[r.kind] += ms;
+      h->t_cnt[r.kind] += 1;
+    }
+    h->ev_pool.push_back({r.a, r.b});
+  }
+  h->pending.clear();
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+void free_dev(void*& p) { if (p) { cudaFree(p); p = nullptr; } }
+template <typename P> void free_devp(P*& p) { if (p) { cudaFree(p); p = nullptr; } }
+
+int dev_alloc(void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) { *p = nullptr; return map_err(e); }
+  return RVE_OK;
+}
+
+// exp(s * 2 pi i j / n) for j < n, FP64 libm, stored as T pairs
+template <typename T> std::vector<T> phase_table(int n, int sgn) {
+  std::vector<T> t(2 * (size_t)n);
+  for (int j = 0; j < n; ++j) {
+    const double a = 2.0 * M_PI * (double)j / (double)n;
+    t[2 * j] = (T)std::cos(a);
+    t[2 * j + 1] = (T)(sgn * std::sin(a));
+  }
+  return t;
+}
+
+template <typename T> int upload_tables(rve_s* h) {
+  for (int a = 0; a < h->dim; ++a) {
+    const int n = h->n[a];
+    std::vector<T> ph = phase_table<T>(n, +1), tw = phase_table<T>(n, -1);
+    int rc = dev_alloc(&h->ph[a], ph.size() * sizeof(T));
+    if (rc) return rc;
+    rc = dev_alloc(&h->tw[a], tw.size() * sizeof(T));
+    if (rc) return rc;
+    CK(cudaMemcpy(h->ph[a], ph.data(), ph.size() * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->tw[a], tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  return RVE_OK;
+}
+
+int64_t spec_elems(const rve_s* h) {
+  return (int64_t)h->kx * h->n[1] * h->n[2];
+}
+
+void free_L(rve_s* h) {
+  free_dev(h->x); free_dev(h->r); free_dev(h->p); free_dev(h->fbuf);
+  free_dev(h->spec); free_dev(h->spec2);
+  free_devp(h->u); free_devp(h->uadj); free_devp(h->part); free_devp(h->cg);
+  free_devp(h->emac_d); free_devp(h->emac_adj_d);
+  if (h->cg_h) { cudaFreeHost(h->cg_h); h->cg_h = nullptr; }
+  h->Lcap = 0;
+}
+
+// Buffers for L load cases (grown, never shrunk).
+int ensure_capacity(rve_s* h, int L) {
+  if (L <= h->Lcap) return RVE_OK;
+  // the adjoint needs the forward u kept, so copy it over
+  double* old_u = h->u;
+  h->u = nullptr;
+  int oldL = h->Lcap;
+  double* keep_u = nullptr;
+  if (old_u && h->solved) {
+    if (cudaMalloc((void**)&keep_u, (size_t)oldL * h->D * h->N * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      h->u = old_u;
+      return RVE_ERR_OOM;
+    }
+    cudaMemcpy(keep_u, old_u, (size_t)oldL * h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice);
+  }
+  if (old_u) cudaFree(old_u);
+  free_L(h);
+  const size_t fld = (size_t)L * h->m * h->N * h->tsize;
+  const size_t sp = (size_t)L * h->m * spec_elems(h) * 2 * h->tsize;
+  int rc = 0;
+  if ((rc = dev_alloc(&h->x, fld)) || (rc = dev_alloc(&h->r, fld)) || (rc = dev_alloc(&h->p, fld)) ||
+      (rc = dev_alloc(&h->fbuf, fld)) || (rc = dev_alloc(&h->spec, sp)))
+    { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
+  if (h->dim == 3 && (rc = dev_alloc(&h->spec2, sp))) { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
+  if ((rc = dev_alloc((void**)&h->u, (size_t)L * h->D * h->N * sizeof(double))) ||
+      (rc = dev_alloc((void**)&h->uadj, (size_t)h->ns * h->D * h->N * sizeof(double))))
+    { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
+  h->part_stride = (int)(h->N / 128 + (int64_t)h->n[1] * h->n[2] * h->m / 2 + 64);
+  const int Lp = L > h->ns ? L : h->ns;
+  if ((rc = dev_alloc((void**)&h->part, (size_t)Lp * h->part_stride * sizeof(double))) ||
+      (rc = dev_alloc((void**)&h->cg, (size_t)Lp * sizeof(CgState))) ||
+      (rc = dev_alloc((void**)&h->emac_d, (size_t)Lp * h->ns * sizeof(double))) ||
+      (rc = dev_alloc((void**)&h->emac_adj_d, (size_t)h->ns * h->ns * sizeof(double))))
+    { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
+  if (cudaMallocHost((void**)&h->cg_h, (size_t)Lp * sizeof(CgState)) != cudaSuccess) {
+    cudaGetLastError(); free_L(h); if (keep_u) cudaFree(keep_u); return RVE_ERR_OOM;
+  }
+  cudaMemset(h->p, 0, fld);
+  cudaMemset(h->x, 0, fld);
+  cudaMemset(h->part, 0, (size_t)Lp * h->part_stride * sizeof(double));
+  if (keep_u) {
+    cudaMemcpy(h->u, keep_u, (size_t)oldL * h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice);
+    cudaFree(keep_u);
+  }
+  h->Lcap = L;
+  CK(cudaGetLastError());
+  return RVE_OK;
+}
+
+template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, const double* emac) {
+  PassArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  for (int i = 0; i < 3; ++i) a.n[i] = h->n[i];
+  a.dim = h->dim; a.L = L; a.m = h->m; a.ns = h->ns; a.nq = h->nq;
+  a.N = h->N; a.kx = h->kx;
+  a.E = (const T*)h->Ein;
+  a.x = (T*)h->x; a.r = (T*)h->r; a.p = (T*)h->p;
+  a.in = (const T*)h->fbuf; a.out = (T*)h->fbuf;
+  a.u64 = u;
+  a.spec = (cplx<T>*)h->spec; a.spec2 = (cplx<T>*)h->spec2;
+  a.emac = emac;
+  for (int i = 0; i < 3; ++i) {
+    a.ph[i] = (const cplx<T>*)h->ph[i];
+    a.tw[i] = (const cplx<T>*)h->tw[i];
+    a.ih[i] = (T)((double)h->n[i] / h->len[i]);
+  }
+  a.lam = (T)h->lam; a.mu2 = (T)h->mu2;
+  a.inv_n = (T)(1.0 / (double)h->N);
+  a.cg = h->cg; a.part = h->part; a.part_stride = h->part_stride;
+  return a;
+}
+
+Fp64Args fp64_args(const rve_s* h, int L, const double* u, const double* emac, CgState* cg) {
+  Fp64Args f;
+  std::memset(&f, 0, sizeof(f));
+  for (int i = 0; i < 3; ++i) { f.n[i] = h->n[i]; f.ih[i] = (double)h->n[i] / h->len[i]; }
+  f.dim = h->dim; f.L = L; f.ns = h->ns; f.nq = h->nq; f.N = h->N;
+  f.E = h->E64; f.u = u; f.emac = emac;
+  f.lam = h->lam; f.mu2 = h->mu2;
+  f.cg = cg; f.part = h->part; f.part_stride = h->part_stride;
+  f.fout = h->fbuf; f.fout_f32 = (h->tsize == 4);
+  return f;
+}
+
+template <typename T> cudaError_t pass_a(rve_s* h, const PassArgs<T>& a) {
+  return timed(h, a.cgphase ? K_A : K_OTHER, [&] {
+    return h->dim == 2 ? launch_pass_a_2d<T>(a, h->stream) : launch_pass_a_3d<T>(a, h->stream);
+  });
+}
+template <typename T> cudaError_t pass_mid(rve_s* h, const PassArgs<T>& a) {
+  const int cg = a.cgphase;
+  if (h->dim == 2) return timed(h, cg ? K_C : K_OTHER, [&] { return launch_pass_c_2d<T>(a, h->stream); });
+  cudaError_t e = timed(h, cg ? K_B : K_OTHER, [&] { return launch_pass_b_3d<T>(a, h->stream); });
+  if (e != cudaSuccess) return e;
+  e = timed(h, cg ? K_C : K_OTHER, [&] { return launch_pass_c_3d<T>(a, h->stream); });
+  if (e != cudaSuccess) return e;
+  return timed(h, cg ? K_D : K_OTHER, [&] { return launch_pass_d_3d<T>(a, h->stream); });
+}
+template <typename T> cudaError_t pass_e(rve_s* h, const PassArgs<T>& a) {
+  return timed(h, a.cgphase ? K_E : K_OTHER, [&] {
+    return h->dim == 2 ? launch_pass_e_2d<T>(a, h->stream) : launch_pass_e_3d<T>(a, h->stream);
+  });
+}
+// One full operator application with the modes set in a.
+template <typename T> cudaError_t apply_passes(rve_s* h, const PassArgs<T>& a) {
+  cudaError_t e = pass_a<T>(h, a);
+  if (e == cudaSuccess) e = pass_mid<T>(h, a);
+  if (e == cudaSuccess) e = pass_e<T>(h, a);
+  return e;
+}
+
+int read_state(rve_s* h, int L) {
+  CK(cudaMemcpyAsync(h->cg_h, h->cg, (size_t)L * sizeof(CgState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) flush_timing(h);
+  return RVE_OK;
+}
+int write_state(rve_s* h, int L) {
+  CK(cudaMemcpyAsync(h->cg, h->cg_h, (size_t)L * sizeof(CgState), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+// The solve driver.  u_out [L][D][N] receives the FP64 nodal fluctuation.
+template <typename T>
+int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max_iter, rve_info* info,
+               double* u_out, double* emac_dev) {
+  const bool mixed = (h->tsize == 4);
+  CK(cudaMemcpyAsync(emac_dev, emac_host, (size_t)L * h->ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(u_out, 0, (size_t)L * h->D * h->N * sizeof(double), h->stream));
+  const double inner_tol = mixed ? std::fmax(rel_tol, 2e-5) : rel_tol;
+  const int max_outer = mixed ? 12 : 6;
+  std::vector<double> f0(L, 0.0), frel(L, 0.0), cgrel(L, 0.0);
+  std::vector<int> iters(L, 0), steps(L, 0), bad(L, 0), active(L, 1);
+  std::memset(h->cg_h, 0, (size_t)L * sizeof(CgState));
+  for (int l = 0; l < L; ++l) { h->cg_h[l].active = 1; h->cg_h[l].status = ST_RUN; }
+  int rc = write_state(h, L);
+  if (rc) return rc;
+
+  Fp64Args fa = fp64_args(h, L, u_out, emac_dev, h->cg);
+  PassArgs<T> a = pass_args<T>(h, L, u_out, emac_dev);
+  const int check_every = 8;
+
+  for (int step = 0;; ++step) {
+    // FP64 residual of the current iterate
+    CK(timed(h, K_RES, [&] { return launch_residual(fa, h->stream); }));
+    if ((rc = read_state(h, L))) return rc;
+    bool any = false;
+    for (int l = 0; l < L; ++l) {
+      if (!active[l]) continue;
+      const double fn2 = h->cg_h[l].fn2;
+      if (step == 0) f0[l] = std::sqrt(fn2);
+      if (!std::isfinite(fn2)) { bad[l] = 1; active[l] = 0; continue; }
+      const double prev = frel[l];
+      frel[l] = (f0[l] > 0.0) ? std::sqrt(fn2) / f0[l] : 0.0;
+      // stop: tolerance met, step or iteration budget spent, or no progress
+      // (round-off floor of the FP64 residual)
+      const bool stalled = step >= 2 && frel[l] > 0.5 * prev;
+      if (frel[l] <= rel_tol || step >= max_outer || iters[l] >= max_iter || stalled) { active[l] = 0; continue; }
+      any = true;
+    }
+    if (!any) break;
+    for (int l = 0; l < L; ++l) {
+      h->cg_h[l].active = active[l];
+      h->cg_h[l].status = ST_RUN;
+      h->cg_h[l].it = 0;
+      h->cg_h[l].maxit = max_iter - iters[l];
+      h->cg_h[l].tol2 = inner_tol * inner_tol;
+      h->cg_h[l].cnt_a = h->cg_h[l].cnt_e = h->cg_h[l].cnt_r = 0;
+    }
+    if ((rc = write_state(h, L))) return rc;
+    // inner right-hand side r0 = -G C (E + B u) from f
+    a.cgphase = 0; a.amode = A_NODAL; a.pmode = P_NODAL_IN; a.emode = E_INIT;
+    a.in = (const T*)h->fbuf;
+    CK(apply_passes<T>(h, a));
+    // projected CG
+    a.cgphase = 1; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
+    for (int it = 0; it < max_iter; it += check_every) {
+      for (int k = 0; k < check_every; ++k) CK(apply_passes<T>(h, a));
+      if ((rc = read_state(h, L))) return rc;
+      bool running = false;
+      for (int l = 0; l < L; ++l)
+        if (active[l] && h->cg_h[l].status == ST_RUN) running = true;
+      if (!running) break;
+    }
+    if ((rc = read_state(h, L))) return rc;
+    for (int l = 0; l < L; ++l) {
+      if (!active[l]) continue;
+      iters[l] += h->cg_h[l].it;
+      steps[l] += 1;
+      cgrel[l] = h->cg_h[l].rr0 > 0 ? std::sqrt(h->cg_h[l].rr / h->cg_h[l].rr0) : 0.0;
+      if (h->cg_h[l].status == ST_BAD) bad[l] = 1;
+    }
+    // u += (B^H B)^-1 B^H delta  (delta = CG iterate x)
+    a.cgphase = 0; a.amode = A_BARE; a.pmode = P_NODAL_OUT; a.emode = E_NODAL;
+    a.in = (const T*)h->x;
+    CK(apply_passes<T>(h, a));
+    for (int l = 0; l < L; ++l)
+      if (bad[l]) { active[l] = 0; h->cg_h[l].active = 0; }
+    if ((rc = write_state(h, L))) return rc;
+  }
+  int worst = RVE_OK;
+  for (int l = 0; l < L; ++l) {
+    int st = RVE_OK;
+    if (bad[l]) st = RVE_ERR_NONFINITE;
+    else if (frel[l] > rel_tol) st = RVE_ERR_NOT_CONVERGED;
+    if (info) {
+      info[l].iterations = iters[l];
+      info[l].refine_steps = steps[l];
+      info[l].status = st;
+      info[l].reserved = 0;
+      info[l].rel_residual = frel[l];
+      info[l].cg_rel_residual = cgrel[l];
+    }
+    if (st == RVE_ERR_NONFINITE || (st != RVE_OK && worst == RVE_OK)) worst = st;
+  }
+  return worst;
+}
+
+int compute_mean_stress(rve_s* h, int L) {
+  // reuse cg[] slots with active = 1 (homogenise does not read them)
+  Fp64Args fa = fp64_args(h, L, h->u, h->emac_d, h->cg);
+  const int nblk = homogenise_blocks(fa);
+  const size_t need = (size_t)L * h->ns * nblk;
+  if ((int)need > h->hpart_cap) {
+    free_devp(h->hpart);
+    int rc = dev_alloc((void**)&h->hpart, need * sizeof(double));
+    if (rc) return rc;
+    h->hpart_cap = (int)need;
+  }
+  int nb = 0;
+  CK(timed(h, K_OTHER, [&] { return launch_homogenise(fa, h->hpart, &nb, h->stream); }));
+  std::vector<double> hp(need);
+  CK(cudaMemcpyAsync(hp.data(), h->hpart, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) flush_timing(h);
+  h->S_h.assign((size_t)L * h->ns, 0.0);
+  const double scale = 1.0 / ((double)h->N * h->nq);
+  for (int l = 0; l < L; ++l)
+    for (int s = 0; s < h->ns; ++s) {
+      double t = 0.0;
+      const double* src = hp.data() + ((size_t)l * h->ns + s) * nb;
+      for (int b = 0; b < nb; ++b) t += src[b];
+      h->S_h[(size_t)l * h->ns + s] = t * scale;
+    }
+  return RVE_OK;
+}
+
+// Gauss-Jordan inverse of a small row-major matrix; false if singular.
+bool invert(int n, const double* A, double* Ainv) {
+  std::vector<double> M((size_t)n * 2 * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) M[i * 2 * n + j] = A[i * n + j];
+    M[i * 2 * n + n + i] = 1.0;
+  }
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i) if (std::fabs(M[i * 2 * n + c]) > std::fabs(M[piv * 2 * n + c])) piv = i;
+    if (std::fabs(M[piv * 2 * n + c]) < 1e-300) return false;
+    if (piv != c) for (int j = 0; j < 2 * n; ++j) std::swap(M[c * 2 * n + j], M[piv * 2 * n + j]);
+    const double d = M[c * 2 * n + c];
+    for (int j = 0; j < 2 * n; ++j) M[c * 2 * n + j] /= d;
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = M[i * 2 * n + c];
+      if (f != 0.0) for (int j = 0; j < 2 * n; ++j) M[i * 2 * n + j] -= f * M[c * 2 * n + j];
+    }
+  }
+  for (int i = 0; i < n; ++i) for (int j = 0; j < n; ++j) Ainv[i * n + j] = M[i * 2 * n + n + j];
+  return true;
+}
+
+__global__ void f32_from_f64(const double* in, float* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+}  // namespace
+
+// ====================================================================
+extern "C" {
+
+const char* rve_error_string(int code) {
+  switch (code) {
+    case RVE_OK: return "ok";
+    case RVE_ERR_ARG: return "invalid argument or call order";
+    case RVE_ERR_UNSUPPORTED_SIZE: return "grid size not supported by the GPU FFT (powers of two, 16..1024 in 2D, 16..256 in 3D)";
+    case RVE_ERR_CUDA: return "CUDA runtime error";
+    case RVE_ERR_OOM: return "device memory allocation failed";
+    case RVE_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
+    case RVE_ERR_NONFINITE: return "non-finite value or CG breakdown";
+    case RVE_ERR_TIMEOUT: return "device-side wait exceeded its limit";
+    default: return "unknown status";
+  }
+}
+
+int rve_create(rve_t* out, int dim, const int64_t* n, const double* length, int precision, void* cuda_stream) {
+  if (!out || !n || (dim != 2 && dim != 3) || (precision != RVE_FP64 && precision != RVE_MIXED)) return RVE_ERR_ARG;
+  *out = nullptr;
+  const int64_t maxn = (dim == 2) ? 1024 : 256;
+  for (int a = 0; a < dim; ++a) {
+    if (!is_pow2(n[a]) || n[a] < 16 || n[a] > maxn) return RVE_ERR_UNSUPPORTED_SIZE;
+    if (length && !(length[a] > 0.0 && std::isfinite(length[a]))) return RVE_ERR_ARG;
+  }
+  rve_s* h = new (std::nothrow) rve_s();
+  if (!h) return RVE_ERR_OOM;
+  h->dim = dim;
+  h->N = 1;
+  for (int a = 0; a < dim; ++a) { h->n[a] = (int)n[a]; h->N *= n[a]; h->len[a] = length ? length[a] : 1.0; }
+  h->precision = precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->ns = dim == 2 ? 3 : 6;
+  h->nq = dim == 2 ? 2 : 6;
+  h->m = h->ns * h->nq;
+  h->D = dim;
+  h->kx = h->n[0] / 2 + 1;
+  h->tsize = precision == RVE_MIXED ? 4 : 8;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); delete h; return RVE_ERR_CUDA; }
+  int rc = precision == RVE_MIXED ? upload_tables<float>(h) : upload_tables<double>(h);
+  if (!rc) rc = dev_alloc((void**)&h->E64, (size_t)h->N * sizeof(double));
+  if (!rc && precision == RVE_MIXED) rc = dev_alloc(&h->Ein, (size_t)h->N * sizeof(float));
+  if (!rc) rc = ensure_capacity(h, 1);
+  if (rc) { rve_destroy(h); return rc; }
+  if (precision == RVE_FP64) h->Ein = h->E64;
+  *out = h;
+  return RVE_OK;
+}
+
+int rve_destroy(rve_t h) {
+  if (!h) return RVE_OK;
+  cudaStreamSynchronize(h->stream);
+  flush_timing(h);
+  for (auto& ev : h->ev_pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  h->ev_pool.clear();
+  free_L(h);
+  if (h->Ein && h->Ein != (void*)h->E64) cudaFree(h->Ein);
+  h->Ein = nullptr;
+  free_devp(h->E64);
+  free_devp(h->hpart);
+  for (int a = 0; a < 3; ++a) { free_dev(h->ph[a]); free_dev(h->tw[a]); }
+  delete h;
+  return RVE_OK;
+}
+
+int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim) {
+  if (!h) return RVE_ERR_ARG;
+  if (n_voxels) *n_voxels = h->N;
+  if (m) *m = h->m;
+  if (n_s) *n_s = h->ns;
+  if (dim) *dim = h->dim;
+  return RVE_OK;
+}
+
+int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_flags) {
+  if (!h || !E || (E_dtype != RVE_F32 && E_dtype != RVE_F64)) return RVE_ERR_ARG;
+  if (!(nu > -1.0 && nu < 0.5)) return RVE_ERR_ARG;
+  std::vector<double> e64((size_t)h->N);
+  if (ptr_flags & RVE_PTR_DEVICE) {
+    if (E_dtype == RVE_F64) {
+      CK(cudaMemcpy(e64.data(), E, (size_t)h->N * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> e32((size_t)h->N);
+      CK(cudaMemcpy(e32.data(), E, (size_t)h->N * sizeof(float), cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < h->N; ++i) e64[i] = e32[i];
+    }
+  } else {
+    if (E_dtype == RVE_F64) std::memcpy(e64.data(), E, (size_t)h->N * sizeof(double));
+    else for (int64_t i = 0; i < h->N; ++i) e64[i] = ((const float*)E)[i];
+  }
+  for (int64_t i = 0; i < h->N; ++i)
+    if (!(e64[i] > 0.0) || !std::isfinite(e64[i])) return RVE_ERR_ARG;
+  CK(cudaMemcpy(h->E64, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice));
+  if (h->precision == RVE_MIXED) {
+    f32_from_f64<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->E64, (float*)h->Ein, h->N);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  h->nu = nu;
+  h->lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));  // unit Young's modulus
+  h->mu2 = 1.0 / (1.0 + nu);
+  h->has_material = true;
+  h->solved = false;
+  return RVE_OK;
+}
+
+int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info) {
+  if (!h || !E_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_iter < 1) return RVE_ERR_ARG;
+  if (!h->has_material) return RVE_ERR_ARG;
+  for (int i = 0; i < L * h->ns; ++i) if (!std::isfinite(E_macro[i])) return RVE_ERR_ARG;
+  h->solved = false;
+  int rc = ensure_capacity(h, L);
+  if (rc) return rc;
+  const int st = (h->precision == RVE_MIXED)
+                     ? solve_impl<float>(h, E_macro, L, rel_tol, max_iter, info, h->u, h->emac_d)
+                     : solve_impl<double>(h, E_macro, L, rel_tol, max_iter, info, h->u, h->emac_d);
+  if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED && st != RVE_ERR_NONFINITE) return st;
+  h->emac_h.assign(E_macro, E_macro + (size_t)L * h->ns);
+  h->L_solved = L;
+  rc = compute_mean_stress(h, L);
+  if (rc) return rc;
+  h->solved = true;
+  return st;
+}
+
+int rve_mean_stress(rve_t h, double* S) {
+  if (!h || !S || !h->solved) return RVE_ERR_ARG;
+  std::memcpy(S, h->S_h.data(), h->S_h.size() * sizeof(double));
+  return RVE_OK;
+}
+
+int rve_effective_tangent(rve_t h, double* C) {
+  if (!h || !C || !h->solved || h->L_solved != h->ns) return RVE_ERR_ARG;
+  const int ns = h->ns;
+  std::vector<double> Minv((size_t)ns * ns);
+  if (!invert(ns, h->emac_h.data(), Minv.data())) return RVE_ERR_ARG;
+  // C[s][t] = sum_l S[l][s] Minv[t][l]   (C = S^T M^-T)
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < ns; ++t) {
+      double v = 0.0;
+      for (int l = 0; l < ns; ++l) v += h->S_h[(size_t)l * ns + s] * Minv[(size_t)t * ns + l];
+      C[s * ns + t] = v;
+    }
+  return RVE_OK;
+}
+
+int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
+  if (!h || !eps || !h->solved || load_case < 0 || load_case >= h->L_solved) return RVE_ERR_ARG;
+  Fp64Args fa = fp64_args(h, h->L_solved, h->u, h->emac_d, h->cg);
+  const size_t bytes = (size_t)h->m * h->N * sizeof(double);
+  double* dst = (double*)eps;
+  double* tmp = nullptr;
+  if (!(ptr_flags & RVE_PTR_DEVICE)) {
+    int rc = dev_alloc((void**)&tmp, bytes);
+    if (rc) return rc;
+    dst = tmp;
+  }
+  cudaError_t e = launch_strain_field(fa, load_case, dst, h->stream);
+  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(eps, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) cudaFree(tmp);
+  return e == cudaSuccess ? RVE_OK : map_err(e);
+}
+
+int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter, void* grad_E, int ptr_flags) {
+  if (!h || !W || !grad_E || !h->solved || h->L_solved != h->ns || !(rel_tol > 0.0) || max_iter < 1)
+    return RVE_ERR_ARG;
+  const int ns = h->ns, L = h->L_solved;
+  std::vector<double> Minv((size_t)ns * ns), Wp((size_t)ns * L, 0.0);
+  if (!invert(ns, h->emac_h.data(), Minv.data())) return RVE_ERR_ARG;
+  for (int a = 0; a < ns; ++a)
+    for (int l = 0; l < L; ++l) {
+      double v = 0.0;
+      for (int b = 0; b < ns; ++b) v += W[a * ns + b] * Minv[(size_t)b * ns + l];
+      Wp[(size_t)a * L + l] = v;
+    }
+  // adjoint solves for the rows of W' that are not zero, macroscopic strain e_a
+  std::vector<int> rows;
+  std::vector<int> has(ns, 0);
+  for (int a = 0; a < ns; ++a)
+    for (int l = 0; l < L; ++l)
+      if (Wp[(size_t)a * L + l] != 0.0) { has[a] = 1; }
+  for (int a = 0; a < ns; ++a) if (has[a]) rows.push_back(a);
+  std::vector<double> ea((size_t)rows.size() * ns, 0.0);
+  for (size_t i = 0; i < rows.size(); ++i) ea[i * ns + rows[i]] = 1.0;
+  int rc = ensure_capacity(h, (int)rows.size());
+  if (rc) return rc;
+  int st = RVE_OK;
+  if (!rows.empty()) {
+    // solve into a temporary [rows][D][N], then scatter to uadj[a]
+    st = (h->precision == RVE_MIXED)
+             ? solve_impl<float>(h, ea.data(), (int)rows.size(), rel_tol, max_iter, nullptr, h->uadj, h->emac_adj_d)
+             : solve_impl<double>(h, ea.data(), (int)rows.size(), rel_tol, max_iter, nullptr, h->uadj, h->emac_adj_d);
+    if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED) return st;
+    // uadj holds the rows compactly in solve order; expand to index a (from the back)
+    for (int i = (int)rows.size() - 1; i >= 0; --i) {
+      if (rows[i] == i) continue;
+      CK(cudaMemcpyAsync(h->uadj + (size_t)rows[i] * h->D * h->N, h->uadj + (size_t)i * h->D * h->N,
+                         (size_t)h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+  }
+  double* Wd = nullptr; int* hasd = nullptr; double* gd = nullptr;
+  if ((rc = dev_alloc((void**)&Wd, Wp.size() * sizeof(double)))) return rc;
+  if ((rc = dev_alloc((void**)&hasd, ns * sizeof(int)))) { cudaFree(Wd); return rc; }
+  const size_t gbytes = (size_t)h->N * sizeof(double);
+  if (!(ptr_flags & RVE_PTR_DEVICE)) {
+    if ((rc = dev_alloc((void**)&gd, gbytes))) { cudaFree(Wd); cudaFree(hasd); return rc; }
+  } else {
+    gd = (double*)grad_E;
+  }
+  cudaError_t e = cudaMemcpyAsync(Wd, Wp.data(), Wp.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hasd, has.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  Fp64Args fa = fp64_args(h, L, h->u, h->emac_d, h->cg);
+  if (e == cudaSuccess) e = launch_adjoint_grad(fa, h->uadj, Wd, hasd, 1.0 / ((double)h->N * h->nq), gd, h->stream);
+  if (e == cudaSuccess && !(ptr_flags & RVE_PTR_DEVICE))
+    e = cudaMemcpyAsync(grad_E, gd, gbytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(Wd); cudaFree(hasd);
+  if (!(ptr_flags & RVE_PTR_DEVICE)) cudaFree(gd);
+  if (e != cudaSuccess) return map_err(e);
+  return st;
+}
+
+int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int ptr_flags) {
+  if (!h || !p || !q) return RVE_ERR_ARG;
+  if (apply_material && !h->has_material) return RVE_ERR_ARG;
+  const size_t bytes = (size_t)h->m * h->N * h->tsize;
+  const cudaMemcpyKind kin = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(h->fbuf, p, bytes, kin, h->stream));
+  std::memset(h->cg_h, 0, sizeof(CgState));
+  h->cg_h[0].active = 1;
+  int rc = write_state(h, 1);
+  if (rc) return rc;
+  h->solved = false;  // the operator shares the solve's buffers
+  if (h->tsize == 4) {
+    PassArgs<float> a = pass_args<float>(h, 1, h->u, h->emac_d);
+    a.amode = apply_material ? A_FIELD : A_BARE; a.pmode = P_G; a.emode = E_OUT;
+    a.in = (const float*)h->fbuf; a.out = (float*)h->x;
+    CK(apply_passes<float>(h, a));
+  } else {
+    PassArgs<double> a = pass_args<double>(h, 1, h->u, h->emac_d);
+    a.amode = apply_material ? A_FIELD : A_BARE; a.pmode = P_G; a.emode = E_OUT;
+    a.in = (const double*)h->fbuf; a.out = (double*)h->x;
+    CK(apply_passes<double>(h, a));
+  }
+  CK(cudaMemcpyAsync(q, h->x, bytes, kout, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+int rve_timing_enable(rve_t h, int enable) {
+  if (!h) return RVE_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  flush_timing(h);
+  h->timing = enable != 0;
+  return RVE_OK;
+}
+
+int rve_timing_read(rve_t h, double* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return RVE_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  flush_timing(h);
+  for (int k = 0; k < RVE_NKINDS; ++k) {
+    ms[k] = h->t_ms[k];
+    launches[k] = h->t_cnt[k];
+    h->t_ms[k] = 0.0;
+    h->t_cnt[k] = 0;
+  }
+  return RVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Host-side declarations shared by the C-ABI translation unit and the kernel
+// translation units (one per dimension and precision).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rve_device.cuh"
+
+namespace rve {
+
+// Modes of the first pass (material + forward x-FFT)
+enum PassAMode {
+  A_CG = 0,      // p <- r + beta p ; sigma = C p ; <p, sigma> -> alpha
+  A_MACRO = 1,   // sigma = C E_macro (broadcast)      (start: r0 = -G C E)
+  A_FIELD = 2,   // sigma = C in  (in = strain field)  (operator application)
+  A_BARE = 3,    // sigma = in (no material)           (bare projection / eps -> u)
+  A_NODAL = 4    // transform the D nodal components of in (FP64 residual -> rhs)
+};
+// Modes of the last pass (inverse x-FFT + update)
+enum PassEMode {
+  E_CG = 0,      // x += alpha p ; r -= alpha q ; <r, r> -> beta, convergence
+  E_INIT = 1,    // r = -q ; x = 0 ; <r, r> -> rr0
+  E_OUT = 2,     // out = q (m components)
+  E_NODAL = 3    // u64 += q (D nodal components, accumulated in FP64)
+};
+// Modes of the projection pass
+enum ProjMode {
+  P_G = 0,       // eps^ = B (B^H B)^-1 B^H sigma^  (m -> m)
+  P_NODAL_IN = 1,  // eps^ = B (B^H B)^-1 f^          (D -> m)
+  P_NODAL_OUT = 2  // u^ = (B^H B)^-1 B^H eps^        (m -> D)
+};
+
+// Everything a pass kernel needs; all pointers are device pointers.
+template <typename T> struct PassArgs {
+  int n[3];          // grid sizes (x, y, z); z = 1 in 2D
+  int dim, L, m, ns, nq;
+  int64_t N;         // voxels
+  int kx;            // n_x/2 + 1
+  const T* E;        // [N] Young's modulus
+  T* x; T* r; T* p;  // [L][m][N] CG vectors
+  const T* in;       // [L][m or D][N] input field (A_FIELD / A_BARE / A_NODAL)
+  T* out;            // [L][m][N] output field (E_OUT)
+  double* u64;       // [L][D][N] FP64 nodal displacement (E_NODAL)
+  cplx<T>* spec;     // first spectrum buffer
+  cplx<T>* spec2;    // second spectrum buffer (3D)
+  const double* emac;  // [L][ns] macroscopic strains
+  const cplx<T>* ph[3];  // exp(2 pi i j / n_a), j < n_a
+  const cplx<T>* tw[3];  // exp(-2 pi i t / n_a), t < n_a
+  T lam, mu2;        // unit-modulus Lame lambda and 2 mu
+  T ih[3];           // inverse voxel sizes
+  T inv_n;           // 1 / N
+  T emac_scale;      // sign/scale for A_MACRO
+  CgState* cg;       // [L]
+  double* part;      // [L][part_stride] block partial sums
+  int part_stride;
+  int amode, emode, pmode;
+  int cgphase;       // 1 inside the CG loop: passes skip load cases whose CG stopped
+  int comp_in;       // number of components in the spectrum for this pass (m or D)
+};
+
+// Arguments of the FP64 real-space kernels (residual, homogenisation, adjoint).
+struct Fp64Args {
+  int n[3];
+  int dim, L, ns, nq;
+  int64_t N;
+  const double* E;      // [N]
+  const double* u;      // [L][D][N] nodal fluctuation displacement
+  const double* emac;   // [L][ns]
+  double ih[3], lam, mu2;
+  CgState* cg;          // [L]
+  double* part;         // [L][part_stride]
+  int part_stride;
+  void* fout;           // [L][D][N] residual in the inner precision
+  int fout_f32;
+};
+
+// Launchers (return cudaError_t of the launch).  Defined per dimension and
+// precision; they pick the template instance for the grid sizes.
+template <typename T> cudaError_t launch_pass_a_2d(const PassArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_pass_c_2d(const PassArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_pass_e_2d(const PassArgs<T>& a, cudaStream_t s);
+
+template <typename T> cudaError_t launch_pass_a_3d(const PassArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_pass_b_3d(const PassArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_pass_c_3d(const PassArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_pass_d_3d(const PassArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_pass_e_3d(const PassArgs<T>& a, cudaStream_t s);
+
+cudaError_t launch_residual(const Fp64Args& a, cudaStream_t s);
+// part[(l*ns + s)*nblk + blk]; returns nblk through *nblk_out
+cudaError_t launch_homogenise(const Fp64Args& a, double* part, int* nblk_out, cudaStream_t s);
+int homogenise_blocks(const Fp64Args& a);
+cudaError_t launch_strain_field(const Fp64Args& a, int l, double* out, cudaStream_t s);
+cudaError_t launch_adjoint_grad(const Fp64Args& a, const double* uadj, const double* W, const int* has_adj,
+                                double scale, double* grad, cudaStream_t s);
+
+// Largest number of blocks per load case any reducing pass uses.
+int max_reduce_blocks(const int* n, int dim, bool fp64);
+
+bool size_supported(const int* n, int dim);
+
+}  // namespace rve

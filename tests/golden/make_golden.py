@@ -1,0 +1,82 @@
+"""Write the stored expected values under tests/golden/ from the FP64 oracle only.
+
+Usage:  python tests/golden/make_golden.py [name ...]
+
+For each named workload (``microstructures.config_inputs``) this runs the
+oracle's projected CG (O1) on the full grid to a relative residual of
+``TOL`` and stores the effective tangent (mean-stress form, Mandel) with the
+iteration counts.  ``disc32`` is also solved by the assembled FEM (O2) and
+both results are stored.  ``lognormal64`` additionally stores the oracle's
+adjoint gradient of J = C_1111 at 16 seeded voxels and its Euler sum.
+Nothing here calls the CUDA path.
+"""
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+TOL = 1e-12
+
+
+def _run(name):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import microstructures as ms
+    from oracle.fe_projection import Problem
+
+    cfg = ms.config_inputs(name)
+    t0 = time.time()
+    P = Problem(cfg["n"], cfg["E"], cfg["nu"])
+    out = dict(name=name, n=list(cfg["n"]), nu=cfg["nu"], tol=TOL,
+               source="oracle.fe_projection.Problem (O1), FP64, numpy FFT")
+    I = np.eye(P.ns)
+    if name == "lognormal64":
+        W = np.zeros((P.ns, P.ns)); W[0, 0] = 1.0
+        grad, C = P.adjoint_gradient(W, tol=TOL)
+        rng = np.random.default_rng(2005)
+        vox = rng.choice(grad.size, size=16, replace=False)
+        out["adjoint_W"] = W.tolist()
+        out["adjoint_voxels"] = [int(v) for v in vox]
+        out["adjoint_grad"] = [float(grad.reshape(-1)[v]) for v in vox]
+        out["adjoint_euler_sum"] = float(np.sum(P.E * grad))
+        out["C_eff"] = C.tolist()
+    else:
+        Em = cfg["E_macro"]
+        if len(Em) == P.ns:
+            C, fields, its = P.effective_tangent(Em, tol=TOL)
+            out["C_eff"] = C.tolist()
+            out["iterations"] = its
+        else:
+            S = []
+            its = []
+            for row in Em:
+                eps, it, _ = P.solve(row, tol=TOL)
+                S.append(P.mean_stress(eps).tolist())
+                its.append(it)
+            out["mean_stress"] = S
+            out["iterations"] = its
+        if name == "disc32":
+            from oracle.fem_assembly import AssembledFEM
+            C2, _ = AssembledFEM(cfg["n"], cfg["E"], cfg["nu"]).effective_tangent(I)
+            out["C_eff_fem"] = C2.tolist()
+            Cf, _, its = P.effective_tangent(I, tol=TOL)
+            out["C_eff"] = Cf.tolist()
+            out["iterations_unit"] = its
+    out["seconds"] = time.time() - t0
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(out, f, indent=1)
+    return name
+
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or ["disc32", "gauss1024", "lognormal64"]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(names)) as pool:
+        for n in pool.imap_unordered(_run, names):
+            print("wrote", n, flush=True)
