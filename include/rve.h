@@ -65,7 +65,8 @@ enum {
   RVE_ERR_OOM = -4,              /* device allocation failed */
   RVE_ERR_NOT_CONVERGED = -5,    /* max_iter reached before the tolerance */
   RVE_ERR_NONFINITE = -6,        /* NaN/Inf or CG breakdown (non-positive curvature) */
-  RVE_ERR_TIMEOUT = -7           /* a device-side wait exceeded its limit */
+  RVE_ERR_TIMEOUT = -7,          /* a device-side wait exceeded its limit */
+  RVE_ERR_SCRATCH_LIMIT = -8     /* grid larger than the static scratch of rve_apply_operator_2d_static */
 };
 
 enum { RVE_FP64 = 0, RVE_MIXED = 1 };          /* precision of rve_create */
@@ -152,6 +153,30 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
 #define RVE_NKINDS 7
 int rve_timing_enable(rve_t h, int enable);
 int rve_timing_read(rve_t h, double* ms /*[RVE_NKINDS]*/, int64_t* launches /*[RVE_NKINDS]*/);
+
+/* Allocation-free operator application (the paper has no counterpart; this is
+ * a service for callers that cannot allocate device memory, e.g. code inside
+ * an application that owns the whole device memory pool through its own
+ * allocator, or latency-critical loops where an allocation may block or fail).
+ * Computes q = G * (C : p) (apply_material = 1) or q = G * p (0) for a 2D grid
+ * in FP32, like rve_apply_operator on an RVE_MIXED handle, without a handle and
+ * without calling cudaMalloc/cudaFree or any allocating routine.
+ *  n[2]       grid sizes, powers of two with 16 <= n <= 256; larger grids
+ *             return RVE_ERR_SCRATCH_LIMIT;
+ *  length[2]  cell lengths (NULL = unit cell);
+ *  E[N]       device pointer, FP32 Young's moduli (may be NULL if apply_material = 0);
+ *  p, q       device pointers, [6][N] FP32 fields (layout as rve_get_strain);
+ *  cuda_stream  stream to run on (NULL = default stream).
+ * Scratch: one static device array of about 1.6 MB (spectrum, tables and a
+ * state record), which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the contents of
+ * the last call (each call rewrites everything it reads), so calls that overlap
+ * on the GPU -- on different streams, or from different host threads -- race;
+ * serialise them.  Returns without waiting for the GPU. */
+int rve_apply_operator_2d_static(const int64_t* n, const double* length, const float* E, double nu,
+                                 const float* p, float* q, int apply_material, void* cuda_stream);
 
 /* Number of voxels N and strain scalars per voxel m of a handle. */
 int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim);

@@ -22,6 +22,7 @@ RVE_ERR_OOM = -4
 RVE_ERR_NOT_CONVERGED = -5
 RVE_ERR_NONFINITE = -6
 RVE_ERR_TIMEOUT = -7
+RVE_ERR_SCRATCH_LIMIT = -8
 RVE_FP64, RVE_MIXED = 0, 1
 RVE_F32, RVE_F64 = 0, 1
 RVE_PTR_HOST, RVE_PTR_DEVICE = 0, 1
@@ -51,6 +52,8 @@ SIGNATURES = {
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "rve_timing_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "rve_apply_operator_2d_static": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_void_p,
+                                               C.c_double, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "rve_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                             C.POINTER(C.c_int)]),
 }

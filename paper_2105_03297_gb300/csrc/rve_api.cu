@@ -453,6 +453,7 @@ const char* rve_error_string(int code) {
     case RVE_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
     case RVE_ERR_NONFINITE: return "non-finite value or CG breakdown";
     case RVE_ERR_TIMEOUT: return "device-side wait exceeded its limit";
+    case RVE_ERR_SCRATCH_LIMIT: return "grid exceeds the static scratch of the allocation-free entry point (n <= 256 per axis)";
     default: return "unknown status";
   }
 }
