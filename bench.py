@@ -32,6 +32,8 @@ WORKLOADS = {
     "gauss1024_fp64": ("gauss1024", "fp64", 1e-11),
     "lognormal64": ("lognormal64", "mixed", 1e-11),
     "spheres128": ("spheres128", "mixed", 1e-11),
+    "lognormal256": ("lognormal256", "mixed", 1e-10),
+    "lognormal256_fp64": ("lognormal256", "fp64", 1e-10),
 }
 
 
@@ -224,11 +226,18 @@ def run_gpu(args):
     E_dev = torch.from_numpy(E.reshape(-1)).cuda()
     r.set_material(E_dev, nu)
     max_iter = 20000
+    ns = 3 if dim == 2 else 6
+
+    def homogenised():
+        # the full tangent when all n_s load cases are solved, else the mean stresses
+        return r.effective_tangent() if L == ns else r.mean_stress()
+
     for _ in range(args.warmup):
         code, info = r.solve(Em, rel_tol=tol, max_iter=max_iter)
-        C = r.effective_tangent()
+        C = homogenised()
     _, C_gold = golden_iterations(cfg_name)
-    acc = float(np.abs(C - np.array(C_gold)).max() / np.abs(np.array(C_gold)).max()) if C_gold else None
+    acc = (float(np.abs(C - np.array(C_gold)).max() / np.abs(np.array(C_gold)).max())
+           if C_gold is not None and L == ns else None)
     r.timing(True)
     r.timing_read()
     iters = []
@@ -240,7 +249,7 @@ def run_gpu(args):
         ev0.record(stream)
         for _ in range(args.steps):
             code, info = r.solve(Em, rel_tol=tol, max_iter=max_iter)
-            C = r.effective_tangent()
+            C = homogenised()
             iters.append([i["iterations"] for i in info])
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -273,7 +282,7 @@ def run_gpu(args):
     for _ in range(args.steps):
         r.set_material(E_host, nu)
         r.solve(Em, rel_tol=tol, max_iter=max_iter)
-        C_h = r.effective_tangent()
+        C_h = homogenised()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     if world > 1:

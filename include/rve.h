@@ -106,7 +106,10 @@ int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_fla
 
 /* Solve L load cases together.  E_macro[L][n_s] (host, Mandel) are the
  * macroscopic strains (the k = 0 mode, Sec. 2.3).  rel_tol bounds the final
- * relative FP64 nodal residual ||B^T C (E + eps~)|| / ||B^T C E||; max_iter
+ * relative FP64 nodal residual ||B^T C (E + eps~)|| / ||B^T C E||; a load case
+ * whose residual reaches the FP64 round-off level of its nodal-force sums
+ * (64 eps times the norm of the summed term magnitudes) also counts as solved,
+ * which covers macroscopic strains that are already in equilibrium; max_iter
  * bounds the projected-CG iterations of each load case.  info[L] (host,
  * may be NULL) receives per-load-case statistics.  Returns the worst status. */
 int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_iter,

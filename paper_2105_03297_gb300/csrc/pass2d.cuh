@@ -9,6 +9,7 @@
 //   E  inverse real FFT along x, then x += alpha p, r -= alpha q and <r, r>
 //      (q never touches memory).
 // DFT convention of Appendix A; the 1/N of the inverse is applied in pass C.
+// Two real rows (y, y+1) share one complex FFT (X_y + i X_{y+1}).
 #pragma once
 #include "rve_internal.h"
 
@@ -16,89 +17,186 @@ namespace rve {
 
 constexpr double kInvSqrt2 = 0.70710678118654752440;
 
+// CG scalars: last-block finalisation of <p, C p> (pass A)
+__device__ __forceinline__ void finish_alpha(CgState* cg, double pq) {
+  cg->pq = pq;
+  if (!(pq > 0.0) || !isfinite(pq)) { cg->status = ST_BAD; cg->alpha = 0.0; }
+  else cg->alpha = cg->rr / pq;
+  cg->cnt_a = 0;
+}
+// ... and of <r, r> (pass E)
+__device__ __forceinline__ void finish_rr(CgState* cg, double rr, bool init) {
+  if (init) {
+    cg->rr0 = rr; cg->rr = rr; cg->it = 0; cg->beta = 0.0;
+    cg->status = !isfinite(rr) ? ST_BAD : (rr == 0.0 ? ST_CONV : ST_RUN);
+  } else {
+    cg->it += 1;
+    if (!isfinite(rr)) { cg->status = ST_BAD; }
+    else {
+      cg->beta = rr / cg->rr;
+      cg->rr = rr;
+      if (rr <= cg->tol2 * cg->rr0) cg->status = ST_CONV;
+      else if (cg->it >= cg->maxit) cg->status = ST_MAXIT;
+    }
+  }
+  cg->cnt_e = 0;
+}
+
+// ------------------------------------------------------------------------
+// Pass A body, shared by 2D (GS = 3 components per element) and 3D (GS = 6):
+// stream TY rows of NX voxels starting at voxel v0 (16-byte vectors, two
+// groups of loads in flight per thread), apply the material, and write the
+// stress of component j into buf[(j*NP + yy/2)*LD + x] (real part for even
+// row yy, imaginary for odd).  Returns this thread's share of <p, C p>.
+template <typename T, int NX, int TY, int GS, int NT, int LD>
+__device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int l, int c0, int64_t v0,
+                                         bool nodal, T beta, bool use_old) {
+  constexpr int VL = Vec16<T>::n;
+  constexpr int NV = TY * NX / VL;
+  constexpr int NP = TY / 2;
+  constexpr int U = 2;
+  const int64_t N = a.N;
+  T acc = 0;
+  for (int base = 0; base < NV; base += U * NT) {
+    T pv[U][GS][VL];
+    T ev[U][VL];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * NT + threadIdx.x;
+      if (i < NV) {
+        const int64_t v = v0 + (int64_t)i * VL;
+        if (nodal) {
+#pragma unroll
+          for (int j = 0; j < GS; ++j) {
+            if (j < a.dim) vload(pv[u][j], a.in + ((int64_t)l * a.dim + j) * N + v);
+            else {
+#pragma unroll
+              for (int q = 0; q < VL; ++q) pv[u][j][q] = 0;
+            }
+          }
+        } else {
+          if (a.amode != A_BARE) vload(ev[u], a.E + v);
+#pragma unroll
+          for (int j = 0; j < GS; ++j) {
+            const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + v;
+            if (a.amode == A_CG) {
+              vload(pv[u][j], a.r + idx);
+              if (use_old) {
+                T po[VL];
+                vload(po, a.p + idx);
+#pragma unroll
+                for (int q = 0; q < VL; ++q) pv[u][j][q] += beta * po[q];
+              }
+            } else if (a.amode == A_MACRO) {
+#pragma unroll
+              for (int q = 0; q < VL; ++q) pv[u][j][q] = (T)a.emac[l * GS + j];
+            } else {
+              vload(pv[u][j], a.in + idx);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * NT + threadIdx.x;
+      if (i < NV) {
+        const int e0 = i * VL;  // element offset inside the tile
+        const int yy = e0 / NX, x0 = e0 % NX;
+        if (!nodal && a.amode == A_CG) {
+          const int64_t v = v0 + (int64_t)e0;
+#pragma unroll
+          for (int j = 0; j < GS; ++j) vstore(a.p + ((int64_t)l * a.m + c0 + j) * N + v, pv[u][j]);
+        }
+#pragma unroll
+        for (int q = 0; q < VL; ++q) {
+          T s[GS];
+          if (nodal || a.amode == A_BARE) {
+#pragma unroll
+            for (int j = 0; j < GS; ++j) s[j] = pv[u][j][q];
+          } else {
+            // isotropic material, unit-modulus Lame constants times E_v
+            T p1[GS];
+#pragma unroll
+            for (int j = 0; j < GS; ++j) p1[j] = pv[u][j][q];
+            constexpr int D = (GS == 3) ? 2 : 3;
+            T tr = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) tr += p1[j];
+            tr *= a.lam;
+            const T e = ev[u][q];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s[j] = e * (tr + a.mu2 * p1[j]);
+#pragma unroll
+            for (int j = D; j < GS; ++j) s[j] = e * (a.mu2 * p1[j]);
+            if (a.amode == A_CG) {
+#pragma unroll
+              for (int j = 0; j < GS; ++j) acc += p1[j] * s[j];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < GS; ++j)
+            reinterpret_cast<T*>(&buf[(j * NP + yy / 2) * LD + x0 + q])[yy & 1] = s[j];
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+// Two-for-one post-processing of the packed rows and transposed store:
+// spectrum element (k, y0 + 2 pr (+1)) of component c0 + j goes to
+// base + j*comp_stride + k*k_stride + 2 pr (+1).
+template <typename T, int NX, int TY, int NT, int LD>
+__device__ __forceinline__ void pass_a_store(const cplx<T>* buf, int gs, cplx<T>* base, int64_t comp_stride,
+                                             int64_t k_stride) {
+  using C = cplx<T>;
+  constexpr int NP = TY / 2;
+  constexpr int KX = NX / 2 + 1;
+  for (int i = threadIdx.x; i < gs * KX * NP; i += NT) {
+    const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
+    const C* row = buf + (j * NP + pr) * LD;
+    const C A = row[k];
+    const C Bc = cconj(row[(NX - k) & (NX - 1)]);
+    const C xa = cscale(cadd(A, Bc), (T)0.5);
+    const C d = csub(A, Bc);
+    const C xb = mkc<T>((T)0.5 * d.y, (T)-0.5 * d.x);
+    C* dst = base + j * comp_stride + (int64_t)k * k_stride + 2 * pr;
+    dst[0] = xa;
+    dst[1] = xb;
+  }
+}
+
 // ---------------------------------------------------------------- pass A
 // grid (n_y/TY, groups, L), groups = n_q element blocks (n_s components each)
 // or one block of D nodal components (A_NODAL).
 template <typename T, int NX, int TY, int NT>
 __global__ void __launch_bounds__(NT) pass_a_2d(PassArgs<T> a) {
   using C = cplx<T>;
-  constexpr int NP = TY / 2;   // two real rows per complex row
-  constexpr int GS = 3;        // components per block (n_s; D = 2 for nodal)
+  constexpr int NP = TY / 2;
+  constexpr int GS = 3;
   constexpr int KX = NX / 2 + 1;
+  constexpr int LD = FftSplit<NX>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [GS][NP][NX]
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [GS][NP][LD]
   __shared__ double red[NT / 32];
   __shared__ int flag;
 
   const int l = blockIdx.z, grp = blockIdx.y, y0 = blockIdx.x * TY;
   const int ny = a.n[1];
-  const int64_t N = a.N;
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
   const bool nodal = (a.amode == A_NODAL);
-  const int gs = nodal ? 2 : 3;
   const int c0 = nodal ? 0 : grp * 3;
   T beta = 0;
   bool use_old = false;
   if (a.amode == A_CG) { beta = (T)cg->beta; use_old = cg->it > 0; }
-  T acc = 0;
-
-  for (int i = threadIdx.x; i < TY * NX; i += NT) {
-    const int yy = i / NX, xx = i % NX;
-    const int64_t v = (int64_t)(y0 + yy) * NX + xx;
-    T s[GS];
-    if (nodal) {
-      s[0] = a.in[((int64_t)l * 2 + 0) * N + v];
-      s[1] = a.in[((int64_t)l * 2 + 1) * N + v];
-      s[2] = 0;
-    } else {
-      T pv[GS];
-#pragma unroll
-      for (int j = 0; j < GS; ++j) {
-        const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + v;
-        if (a.amode == A_CG) {
-          T t = a.r[idx];
-          if (use_old) t += beta * a.p[idx];
-          a.p[idx] = t;
-          pv[j] = t;
-        } else if (a.amode == A_MACRO) {
-          pv[j] = (T)a.emac[l * 3 + j];
-        } else {
-          pv[j] = a.in[idx];
-        }
-      }
-      if (a.amode == A_BARE) {
-        s[0] = pv[0]; s[1] = pv[1]; s[2] = pv[2];
-      } else {
-        const T e = a.E[v];
-        const T tr = a.lam * (pv[0] + pv[1]);
-        s[0] = e * (tr + a.mu2 * pv[0]);
-        s[1] = e * (tr + a.mu2 * pv[1]);
-        s[2] = e * (a.mu2 * pv[2]);
-      }
-      if (a.amode == A_CG) acc += pv[0] * s[0] + pv[1] * s[1] + pv[2] * s[2];
-    }
-#pragma unroll
-    for (int j = 0; j < GS; ++j)
-      reinterpret_cast<T*>(&buf[(j * NP + yy / 2) * NX + xx])[yy & 1] = s[j];
-  }
+  const T acc = pass_a_load<T, NX, TY, GS, NT, LD>(a, buf, l, c0, (int64_t)y0 * NX, nodal, beta, use_old);
   __syncthreads();
-  smem_fft<T, NX, GS * NP, NX, NT, -1>(buf, a.tw[0]);
-
-  // two-for-one real FFT: rows (y, y+1) were packed as Z = X_y + i X_{y+1}
-  for (int i = threadIdx.x; i < gs * KX * NP; i += NT) {
-    const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
-    const C* row = buf + (j * NP + pr) * NX;
-    const C A = row[k];
-    const C Bc = cconj(row[(NX - k) & (NX - 1)]);
-    const C xa = cscale(cadd(A, Bc), (T)0.5);
-    const C d = csub(A, Bc);
-    const C xb = mkc<T>((T)0.5 * d.y, (T)-0.5 * d.x);
-    C* dst = a.spec + (((int64_t)l * a.m + c0 + j) * KX + k) * ny + y0 + 2 * pr;
-    dst[0] = xa;
-    dst[1] = xb;
-  }
+  smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
+  pass_a_store<T, NX, TY, NT, LD>(buf, nodal ? 2 : 3, a.spec + (((int64_t)l * a.m + c0) * KX) * ny + y0,
+                                  (int64_t)KX * ny, ny);
 
   if (a.amode == A_CG) {
     const double s = block_sum<NT>((double)acc, red);
@@ -107,12 +205,7 @@ __global__ void __launch_bounds__(NT) pass_a_2d(PassArgs<T> a) {
     double* part = a.part + (int64_t)l * a.part_stride;
     if (publish_partial(s, part, &cg->cnt_a, blk, nblk, &flag)) {
       const double pq = sum_partials<NT>(part, nblk, red);
-      if (threadIdx.x == 0) {
-        cg->pq = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) { cg->status = ST_BAD; cg->alpha = 0.0; }
-        else cg->alpha = cg->rr / pq;
-        cg->cnt_a = 0;
-      }
+      if (threadIdx.x == 0) finish_alpha(cg, pq);
     }
   }
 }
@@ -174,8 +267,9 @@ template <typename T, int NY, int NT>
 __global__ void __launch_bounds__(NT) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 6;
+  constexpr int LD = FftSplit<NY>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [M][NY]
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [M][LD]
   const int kx = blockIdx.x, l = blockIdx.y;
   const int KX = a.kx;
   CgState* cg = a.cg + l;
@@ -183,19 +277,20 @@ __global__ void __launch_bounds__(NT) pass_c_2d(PassArgs<T> a) {
   if (a.cgphase && cg->status != ST_RUN) return;
   const int cin = (a.pmode == P_NODAL_IN) ? 2 : M;
   const int cout = (a.pmode == P_NODAL_OUT) ? 2 : M;
+  const C* src = a.spec + (((int64_t)l * M) * KX + kx) * NY;
   for (int i = threadIdx.x; i < cin * NY; i += NT) {
     const int c = i / NY, y = i % NY;
-    buf[c * NY + y] = a.spec[(((int64_t)l * M + c) * KX + kx) * NY + y];
+    buf[c * LD + y] = src[(int64_t)c * KX * NY + y];
   }
   __syncthreads();
-  if (cin == M) smem_fft<T, NY, M, NY, NT, -1>(buf, a.tw[1]);
-  else smem_fft<T, NY, 2, NY, NT, -1>(buf, a.tw[1]);
+  if (cin == M) smem_fft<T, NY, M, LD, NT, -1>(buf, a.tw[1]);
+  else smem_fft<T, NY, 2, LD, NT, -1>(buf, a.tw[1]);
 
   const C ex = a.ph[0][kx];
   for (int ky = threadIdx.x; ky < NY; ky += NT) {
     C s[M];
 #pragma unroll
-    for (int c = 0; c < M; ++c) s[c] = (c < cin) ? buf[c * NY + ky] : mkc<T>(0, 0);
+    for (int c = 0; c < M; ++c) s[c] = (c < cin) ? buf[c * LD + ky] : mkc<T>(0, 0);
     if (kx == 0 && ky == 0) {
 #pragma unroll
       for (int c = 0; c < M; ++c) s[c] = mkc<T>(0, 0);
@@ -204,71 +299,138 @@ __global__ void __launch_bounds__(NT) pass_c_2d(PassArgs<T> a) {
     }
 #pragma unroll
     for (int c = 0; c < M; ++c)
-      if (c < cout) buf[c * NY + ky] = s[c];
+      if (c < cout) buf[c * LD + ky] = s[c];
   }
   __syncthreads();
-  if (cout == M) smem_fft<T, NY, M, NY, NT, +1>(buf, a.tw[1]);
-  else smem_fft<T, NY, 2, NY, NT, +1>(buf, a.tw[1]);
+  if (cout == M) smem_fft<T, NY, M, LD, NT, +1>(buf, a.tw[1]);
+  else smem_fft<T, NY, 2, LD, NT, +1>(buf, a.tw[1]);
+  C* dst = a.spec + (((int64_t)l * M) * KX + kx) * NY;
   for (int i = threadIdx.x; i < cout * NY; i += NT) {
     const int c = i / NY, y = i % NY;
-    a.spec[(((int64_t)l * M + c) * KX + kx) * NY + y] = buf[c * NY + y];
+    dst[(int64_t)c * KX * NY + y] = buf[c * LD + y];
   }
 }
 
+// ------------------------------------------------------------------------
+// Pass E body shared by 2D and 3D: load the (k, y-pair) spectra of ge
+// components into packed rows (component j at src + j*comp_stride +
+// k*k_stride + y-offset, rows j*NP + pr), ready for the inverse FFT.
+template <typename T, int NX, int TY, int NT, int LD>
+__device__ __forceinline__ void pass_e_unpack(cplx<T>* buf, const cplx<T>* src, int ge, int64_t comp_stride,
+                                              int64_t k_stride) {
+  using C = cplx<T>;
+  constexpr int NP = TY / 2;
+  constexpr int KX = NX / 2 + 1;
+  for (int i = threadIdx.x; i < ge * KX * NP; i += NT) {
+    const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
+    const C* s = src + j * comp_stride + (int64_t)k * k_stride + 2 * pr;
+    C xa = s[0], xb = s[1];
+    if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }  // C2R ignores these imaginary parts
+    C* row = buf + (j * NP + pr) * LD;
+    row[k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);                                  // X_a + i X_b
+    if (k > 0 && k < NX / 2) row[NX - k] = mkc<T>(xa.x + xb.y, xb.x - xa.y);    // conj(X_a) + i conj(X_b)
+  }
+}
+
+// Per-voxel update of ge components over the tile of TY rows starting at
+// voxel v0; q of component j comes from the packed rows j*NP...  idx0 /
+// uidx0: offsets of the first component's [N] slab in the CG vectors / the
+// FP64 nodal field (components follow at stride N).  Returns the thread's
+// share of <r, r>.
+template <typename T, int NX, int TY, int NT, int LD>
+__device__ __forceinline__ T pass_e_update(const PassArgs<T>& a, const cplx<T>* buf, int ge, int64_t v0,
+                                           int64_t idx0, int64_t uidx0, T alpha) {
+  constexpr int VL = Vec16<T>::n;
+  constexpr int NV = TY * NX / VL;
+  constexpr int NP = TY / 2;
+  constexpr int U = 2;
+  T acc = 0;
+  for (int base = 0; base < ge * NV; base += U * NT) {
+    T q[U][VL], xv[U][VL], rv[U][VL], pv[U][VL];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * NT + threadIdx.x;
+      if (i < ge * NV) {
+        const int j = i / NV, e0 = (i % NV) * VL;
+        const int yy = e0 / NX, x0 = e0 % NX;
+#pragma unroll
+        for (int w = 0; w < VL; ++w)
+          q[u][w] = reinterpret_cast<const T*>(&buf[(j * NP + yy / 2) * LD + x0 + w])[yy & 1];
+        if (a.emode == E_CG) {
+          const int64_t idx = idx0 + (int64_t)j * a.N + v0 + e0;
+          vload(xv[u], a.x + idx);
+          vload(rv[u], a.r + idx);
+          vload(pv[u], a.p + idx);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * NT + threadIdx.x;
+      if (i < ge * NV) {
+        const int j = i / NV, e0 = (i % NV) * VL;
+        const int64_t idx = idx0 + (int64_t)j * a.N + v0 + e0;
+        if (a.emode == E_CG) {
+#pragma unroll
+          for (int w = 0; w < VL; ++w) {
+            xv[u][w] += alpha * pv[u][w];
+            rv[u][w] -= alpha * q[u][w];
+            acc += rv[u][w] * rv[u][w];
+          }
+          vstore(a.x + idx, xv[u]);
+          vstore(a.r + idx, rv[u]);
+        } else if (a.emode == E_INIT) {
+#pragma unroll
+          for (int w = 0; w < VL; ++w) {
+            rv[u][w] = -q[u][w];
+            xv[u][w] = 0;
+            acc += rv[u][w] * rv[u][w];
+          }
+          vstore(a.r + idx, rv[u]);
+          vstore(a.x + idx, xv[u]);
+        } else if (a.emode == E_OUT) {
+          vstore(a.out + idx, q[u]);
+        } else {  // E_NODAL: accumulate the displacement correction in FP64
+          double* u64 = a.u64 + uidx0 + (int64_t)j * a.N + v0 + e0;
+#pragma unroll
+          for (int w = 0; w < VL; ++w) u64[w] += (double)q[u][w];
+        }
+      }
+    }
+  }
+  return acc;
+}
+
 // ---------------------------------------------------------------- pass E
-// grid (n_y/TY, components, L); inverse real FFT along x of one component.
+// grid (n_y/TY, groups, L): groups = n_q elements (3 components each) or one
+// group of the D = 2 nodal components (E_NODAL); inverse real FFT along x.
 template <typename T, int NX, int TY, int NT>
 __global__ void __launch_bounds__(NT) pass_e_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
+  constexpr int GE = 3;
+  constexpr int LD = FftSplit<NX>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [NP][NX]
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [GE][NP][LD]
   __shared__ double red[NT / 32];
   __shared__ int flag;
-  const int l = blockIdx.z, c = blockIdx.y, y0 = blockIdx.x * TY;
+  const int l = blockIdx.z, grp = blockIdx.y, y0 = blockIdx.x * TY;
   const int ny = a.n[1];
   const int64_t N = a.N;
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
+  const bool nodal = (a.emode == E_NODAL);
+  const int ge = nodal ? 2 : GE;
+  const int c0 = nodal ? 0 : grp * GE;
 
-  for (int i = threadIdx.x; i < KX * NP; i += NT) {
-    const int pr = i % NP, k = i / NP;
-    const C* src = a.spec + (((int64_t)l * a.m + c) * KX + k) * ny + y0 + 2 * pr;
-    C xa = src[0], xb = src[1];
-    if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }  // C2R ignores these imaginary parts
-    buf[pr * NX + k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);           // X_a + i X_b
-    if (k > 0 && k < NX / 2) buf[pr * NX + NX - k] = mkc<T>(xa.x + xb.y, xb.x - xa.y);  // conj(X_a) + i conj(X_b)
-  }
+  pass_e_unpack<T, NX, TY, NT, LD>(buf, a.spec + (((int64_t)l * a.m + c0) * KX) * ny + y0, ge, (int64_t)KX * ny, ny);
   __syncthreads();
-  smem_fft<T, NX, NP, NX, NT, +1>(buf, a.tw[0]);
-
-  T acc = 0;
+  smem_fft<T, NX, GE * NP, LD, NT, +1>(buf, a.tw[0]);
   const T alpha = (a.emode == E_CG) ? (T)cg->alpha : (T)0;
-  for (int i = threadIdx.x; i < TY * NX; i += NT) {
-    const int yy = i / NX, xx = i % NX;
-    const int64_t v = (int64_t)(y0 + yy) * NX + xx;
-    const T q = reinterpret_cast<const T*>(&buf[(yy / 2) * NX + xx])[yy & 1];
-    if (a.emode == E_NODAL) {
-      a.u64[((int64_t)l * 2 + c) * N + v] += (double)q;
-      continue;
-    }
-    const int64_t idx = ((int64_t)l * a.m + c) * N + v;
-    if (a.emode == E_CG) {
-      a.x[idx] += alpha * a.p[idx];
-      const T rv = a.r[idx] - alpha * q;
-      a.r[idx] = rv;
-      acc += rv * rv;
-    } else if (a.emode == E_INIT) {
-      const T rv = -q;
-      a.r[idx] = rv;
-      a.x[idx] = 0;
-      acc += rv * rv;
-    } else {
-      a.out[idx] = q;
-    }
-  }
+  const T acc = pass_e_update<T, NX, TY, NT, LD>(a, buf, ge, (int64_t)y0 * NX, ((int64_t)l * a.m + c0) * N,
+                                                 (int64_t)l * 2 * N, alpha);
 
   if (a.emode == E_CG || a.emode == E_INIT) {
     const double s = block_sum<NT>((double)acc, red);
@@ -277,22 +439,7 @@ __global__ void __launch_bounds__(NT) pass_e_2d(PassArgs<T> a) {
     double* part = a.part + (int64_t)l * a.part_stride;
     if (publish_partial(s, part, &cg->cnt_e, blk, nblk, &flag)) {
       const double rr = sum_partials<NT>(part, nblk, red);
-      if (threadIdx.x == 0) {
-        if (a.emode == E_INIT) {
-          cg->rr0 = rr; cg->rr = rr; cg->it = 0; cg->beta = 0.0;
-          cg->status = !isfinite(rr) ? ST_BAD : (rr == 0.0 ? ST_CONV : ST_RUN);
-        } else {
-          cg->it += 1;
-          if (!isfinite(rr)) { cg->status = ST_BAD; }
-          else {
-            cg->beta = rr / cg->rr;
-            cg->rr = rr;
-            if (rr <= cg->tol2 * cg->rr0) cg->status = ST_CONV;
-            else if (cg->it >= cg->maxit) cg->status = ST_MAXIT;
-          }
-        }
-        cg->cnt_e = 0;
-      }
+      if (threadIdx.x == 0) finish_rr(cg, rr, a.emode == E_INIT);
     }
   }
 }
@@ -304,8 +451,9 @@ template <> struct Tile2D<double> { static constexpr int TY = 4; };
 
 template <typename T, int NX>
 cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile2D<T>::TY, NT = 256;
-  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * NX;
+  constexpr int TY = Tile2D<T>::TY;
+  constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
+  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_2d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
@@ -315,19 +463,20 @@ cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
 }
 template <typename T, int NX>
 cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile2D<T>::TY, NT = 256;
-  const size_t sm = sizeof(cplx<T>) * (TY / 2) * NX;
+  constexpr int TY = Tile2D<T>::TY;
+  constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
+  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_2d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.emode == E_NODAL ? 2 : 6, a.L);
+  dim3 grid(a.n[1] / TY, a.emode == E_NODAL ? 1 : 2, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int NY>
 cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int NT = (NY >= 512) ? 512 : 256;
-  const size_t sm = sizeof(cplx<T>) * 6 * NY;
+  constexpr int NT = fft_threads<NY, 6>();
+  const size_t sm = sizeof(cplx<T>) * 6 * FftSplit<NY>::LD;
   auto k = pass_c_2d<T, NY, NT>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
@@ -359,4 +508,3 @@ template <typename T> cudaError_t launch_pass_c_2d(const PassArgs<T>& a, cudaStr
 }
 
 }  // namespace rve
-

@@ -55,12 +55,12 @@ __global__ void __launch_bounds__(NT) residual_2d(Fp64Args a) {
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   const int64_t n = (int64_t)blockIdx.x * NT + threadIdx.x;
-  double acc = 0.0;
+  double acc = 0.0, acca = 0.0;
   if (n < a.N) {
     const int x = (int)(n % a.n[0]), y = (int)(n / a.n[0]);
     const double* u = a.u + (int64_t)l * 2 * a.N;
     const double* em = a.emac + l * 3;
-    double fx = 0.0, fy = 0.0;
+    double fx = 0.0, fy = 0.0, ax = 0.0, ay = 0.0;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -81,15 +81,20 @@ __global__ void __launch_bounds__(NT) residual_2d(Fp64Args a) {
           const double sxy = kInvSqrt2 * sig[2];
           fx += g0x * sig[0] + g0y * sxy;
           fy += g0x * sxy + g0y * sig[1];
+          ax += fabs(g0x * sig[0]) + fabs(g0y * sxy);
+          ay += fabs(g0x * sxy) + fabs(g0y * sig[1]);
         }
         if (in1) {
           stress_2d(eps[1], e, a.lam, a.mu2, sig);
           const double sxy = kInvSqrt2 * sig[2];
           fx += g1x * sig[0] + g1y * sxy;
           fy += g1x * sxy + g1y * sig[1];
+          ax += fabs(g1x * sig[0]) + fabs(g1y * sxy);
+          ay += fabs(g1x * sxy) + fabs(g1y * sig[1]);
         }
       }
     acc = fx * fx + fy * fy;
+    acca = ax * ax + ay * ay;
     if (a.fout_f32) {
       float* f = (float*)a.fout + (int64_t)l * 2 * a.N;
       f[n] = (float)fx; f[a.N + n] = (float)fy;
@@ -99,10 +104,14 @@ __global__ void __launch_bounds__(NT) residual_2d(Fp64Args a) {
     }
   }
   const double s = block_sum<NT>(acc, red);
+  const double sa = block_sum<NT>(acca, red);
   double* part = a.part + (int64_t)l * a.part_stride;
+  double* parta = part + a.part_stride / 2;
+  if (threadIdx.x == 0) parta[blockIdx.x] = sa;
   if (publish_partial(s, part, &cg->cnt_r, blockIdx.x, gridDim.x, &flag)) {
     const double t = sum_partials<NT>(part, gridDim.x, red);
-    if (threadIdx.x == 0) { cg->fn2 = t; cg->cnt_r = 0; }
+    const double ta = sum_partials<NT>(parta, gridDim.x, red);
+    if (threadIdx.x == 0) { cg->fn2 = t; cg->fa2 = ta; cg->cnt_r = 0; }
   }
 }
 

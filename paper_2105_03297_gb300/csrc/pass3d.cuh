@@ -25,15 +25,6 @@ __host__ __device__ constexpr int kuhn_perm(int t, int i) {
                   : (i == 0 ? 2 : i == 1 ? 1 : 0);
 }
 
-// Mandel material sigma = e * (lam tr(eps) 1 + 2 mu eps)
-template <typename T> __device__ __forceinline__ void material6(const T* p, T e, T lam, T mu2, T* s) {
-  const T tr = lam * (p[0] + p[1] + p[2]);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) s[j] = e * (tr + mu2 * p[j]);
-#pragma unroll
-  for (int j = 3; j < 6; ++j) s[j] = e * (mu2 * p[j]);
-}
-
 // ---------------------------------------------------------------- pass A
 // grid (n_y/TY, n_z, L*G), G = 6 tetrahedra (6 components each) or 1 (nodal, 3).
 template <typename T, int NX, int TY, int NT>
@@ -42,8 +33,9 @@ __global__ void __launch_bounds__(NT) pass_a_3d(PassArgs<T> a) {
   constexpr int NP = TY / 2;
   constexpr int GS = 6;
   constexpr int KX = NX / 2 + 1;
+  constexpr int LD = FftSplit<NX>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [GS][NP][NX]
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [GS][NP][LD]
   __shared__ double red[NT / 32];
   __shared__ int flag;
   const bool nodal = (a.amode == A_NODAL);
@@ -51,72 +43,20 @@ __global__ void __launch_bounds__(NT) pass_a_3d(PassArgs<T> a) {
   const int l = blockIdx.z / G, grp = blockIdx.z % G;
   const int z = blockIdx.y, y0 = blockIdx.x * TY;
   const int ny = a.n[1], nz = a.n[2];
-  const int64_t N = a.N;
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
-  const int gs = nodal ? 3 : 6;
   const int c0 = nodal ? 0 : grp * 6;
   T beta = 0;
   bool use_old = false;
   if (a.amode == A_CG) { beta = (T)cg->beta; use_old = cg->it > 0; }
-  T acc = 0;
-  const int64_t base_v = ((int64_t)z * ny + y0) * NX;
-
-  for (int i = threadIdx.x; i < TY * NX; i += NT) {
-    const int yy = i / NX, xx = i % NX;
-    const int64_t v = base_v + i;
-    T s[GS];
-    if (nodal) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) s[j] = a.in[((int64_t)l * 3 + j) * N + v];
-      s[3] = s[4] = s[5] = 0;
-    } else {
-      T pv[GS];
-#pragma unroll
-      for (int j = 0; j < GS; ++j) {
-        const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + v;
-        if (a.amode == A_CG) {
-          T t = a.r[idx];
-          if (use_old) t += beta * a.p[idx];
-          a.p[idx] = t;
-          pv[j] = t;
-        } else if (a.amode == A_MACRO) {
-          pv[j] = (T)a.emac[l * 6 + j];
-        } else {
-          pv[j] = a.in[idx];
-        }
-      }
-      if (a.amode == A_BARE) {
-#pragma unroll
-        for (int j = 0; j < GS; ++j) s[j] = pv[j];
-      } else {
-        material6<T>(pv, a.E[v], a.lam, a.mu2, s);
-      }
-      if (a.amode == A_CG) {
-#pragma unroll
-        for (int j = 0; j < GS; ++j) acc += pv[j] * s[j];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < GS; ++j)
-      reinterpret_cast<T*>(&buf[(j * NP + yy / 2) * NX + xx])[yy & 1] = s[j];
-  }
+  const T acc = pass_a_load<T, NX, TY, GS, NT, LD>(a, buf, l, c0, ((int64_t)z * ny + y0) * NX, nodal, beta,
+                                                   use_old);
   __syncthreads();
-  smem_fft<T, NX, GS * NP, NX, NT, -1>(buf, a.tw[0]);
-
-  for (int i = threadIdx.x; i < gs * KX * NP; i += NT) {
-    const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
-    const C* row = buf + (j * NP + pr) * NX;
-    const C A = row[k];
-    const C Bc = cconj(row[(NX - k) & (NX - 1)]);
-    const C xa = cscale(cadd(A, Bc), (T)0.5);
-    const C d = csub(A, Bc);
-    const C xb = mkc<T>((T)0.5 * d.y, (T)-0.5 * d.x);
-    C* dst = a.spec + ((((int64_t)l * a.m + c0 + j) * KX + k) * nz + z) * ny + y0 + 2 * pr;
-    dst[0] = xa;
-    dst[1] = xb;
-  }
+  smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
+  pass_a_store<T, NX, TY, NT, LD>(buf, nodal ? 3 : 6,
+                                  a.spec + ((((int64_t)l * a.m + c0) * KX) * nz + z) * ny + y0,
+                                  (int64_t)KX * nz * ny, (int64_t)nz * ny);
 
   if (a.amode == A_CG) {
     const double s = block_sum<NT>((double)acc, red);
@@ -125,12 +65,7 @@ __global__ void __launch_bounds__(NT) pass_a_3d(PassArgs<T> a) {
     double* part = a.part + (int64_t)l * a.part_stride;
     if (publish_partial(s, part, &cg->cnt_a, blk, nblk, &flag)) {
       const double pq = sum_partials<NT>(part, nblk, red);
-      if (threadIdx.x == 0) {
-        cg->pq = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) { cg->status = ST_BAD; cg->alpha = 0.0; }
-        else cg->alpha = cg->rr / pq;
-        cg->cnt_a = 0;
-      }
+      if (threadIdx.x == 0) finish_alpha(cg, pq);
     }
   }
 }
@@ -142,7 +77,8 @@ template <typename T, int NY, int TZB, int NT, bool FWD>
 __global__ void __launch_bounds__(NT) pass_y_3d(PassArgs<T> a, int Cc) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [TZB][NY]
+  constexpr int LD = FftSplit<NY>::LD;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [TZB][LD]
   const int l = blockIdx.z / Cc, c = blockIdx.z % Cc;
   const int kx = blockIdx.y, z0 = blockIdx.x * TZB;
   const int nz = a.n[2], KX = a.kx;
@@ -152,47 +88,52 @@ __global__ void __launch_bounds__(NT) pass_y_3d(PassArgs<T> a, int Cc) {
   const int64_t cbase = (((int64_t)l * a.m + c) * KX + kx);
   if (FWD) {
     const C* src = a.spec + (cbase * nz + z0) * NY;
-    for (int i = threadIdx.x; i < TZB * NY; i += NT) buf[i] = src[i];
+    for (int i = threadIdx.x; i < TZB * NY; i += NT) buf[(i / NY) * LD + (i % NY)] = src[i];
   } else {
     const C* src = a.spec2 + cbase * NY * nz + z0;
     for (int i = threadIdx.x; i < TZB * NY; i += NT) {
       const int zz = i % TZB, ky = i / TZB;
-      buf[zz * NY + ky] = src[(int64_t)ky * nz + zz];
+      buf[zz * LD + ky] = src[(int64_t)ky * nz + zz];
     }
   }
   __syncthreads();
-  smem_fft<T, NY, TZB, NY, NT, FWD ? -1 : +1>(buf, a.tw[1]);
+  smem_fft<T, NY, TZB, LD, NT, FWD ? -1 : +1>(buf, a.tw[1]);
   if (FWD) {
     C* dst = a.spec2 + cbase * NY * nz + z0;
     for (int i = threadIdx.x; i < TZB * NY; i += NT) {
       const int zz = i % TZB, ky = i / TZB;
-      dst[(int64_t)ky * nz + zz] = buf[zz * NY + ky];
+      dst[(int64_t)ky * nz + zz] = buf[zz * LD + ky];
     }
   } else {
     C* dst = a.spec + (cbase * nz + z0) * NY;
-    for (int i = threadIdx.x; i < TZB * NY; i += NT) dst[i] = buf[i];
+    for (int i = threadIdx.x; i < TZB * NY; i += NT) dst[i] = buf[(i / NY) * LD + (i % NY)];
   }
 }
 
 // ---------------------------------------------------------------- pass C
-// Projection of the 36 spectra at one wavevector (modes as in 2D).
-template <typename T>
-__device__ __forceinline__ void project_3d(cplx<T>* s, const cplx<T>* e, const T* ih, T scale, int mode) {
+// Projection at one wavevector of the column kz of buf ([36][LD] in shared
+// memory), in place, streaming the components so that only the element
+// gradients, B^H B and t live in registers.
+//   mode P_G:         s (36) -> B (B^H B)^-1 B^H s
+//   mode P_NODAL_IN:  rows 0..2 = f^ -> B (B^H B)^-1 f^   (36 out)
+//   mode P_NODAL_OUT: s (36) -> (B^H B)^-1 B^H s           (3 out, rows 0..2)
+template <typename T, int LD>
+__device__ __forceinline__ void project_3d(cplx<T>* col, const cplx<T>* e, const T* ih, T scale, int mode) {
   using C = cplx<T>;
   const C one = mkc<T>(1, 0);
   C d[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) d[i] = cscale(csub(e[i], one), ih[i]);
   const C e01 = cmul(e[0], e[1]), e02 = cmul(e[0], e[2]), e12 = cmul(e[1], e[2]);
-  // element gradients g[t][axis]
+  // element gradients g[t][axis] of the Kuhn tetrahedra {0, e_a, e_a+e_b, 1}
   C g[6][3];
-  g[0][0] = d[0];           g[0][1] = cmul(e[0], d[1]);  g[0][2] = cmul(e01, d[2]);   // (x,y,z)
-  g[1][0] = d[0];           g[1][1] = cmul(e02, d[1]);   g[1][2] = cmul(e[0], d[2]);  // (x,z,y)
-  g[2][0] = cmul(e[1], d[0]); g[2][1] = d[1];            g[2][2] = cmul(e01, d[2]);   // (y,x,z)
-  g[3][0] = cmul(e12, d[0]);  g[3][1] = d[1];            g[3][2] = cmul(e[1], d[2]);  // (y,z,x)
-  g[4][0] = cmul(e[2], d[0]); g[4][1] = cmul(e02, d[1]); g[4][2] = d[2];              // (z,x,y)
-  g[5][0] = cmul(e12, d[0]);  g[5][1] = cmul(e[2], d[1]); g[5][2] = d[2];             // (z,y,x)
-  // M = 1/2 sum_t (|g|^2 I + g g^H)
+  g[0][0] = d[0];             g[0][1] = cmul(e[0], d[1]);  g[0][2] = cmul(e01, d[2]);   // (x,y,z)
+  g[1][0] = d[0];             g[1][1] = cmul(e02, d[1]);   g[1][2] = cmul(e[0], d[2]);  // (x,z,y)
+  g[2][0] = cmul(e[1], d[0]); g[2][1] = d[1];              g[2][2] = cmul(e01, d[2]);   // (y,x,z)
+  g[3][0] = cmul(e12, d[0]);  g[3][1] = d[1];              g[3][2] = cmul(e[1], d[2]);  // (y,z,x)
+  g[4][0] = cmul(e[2], d[0]); g[4][1] = cmul(e02, d[1]);   g[4][2] = d[2];              // (z,x,y)
+  g[5][0] = cmul(e12, d[0]);  g[5][1] = cmul(e[2], d[1]);  g[5][2] = d[2];              // (z,y,x)
+  // M = B^H B = 1/2 sum_t (|g|^2 I + g g^H)
   T mdiag[3] = {0, 0, 0};
   C m01 = mkc<T>(0, 0), m02 = mkc<T>(0, 0), m12 = mkc<T>(0, 0);
 #pragma unroll
@@ -206,50 +147,53 @@ __device__ __forceinline__ void project_3d(cplx<T>* s, const cplx<T>* e, const T
     m02 = cadd(m02, cscale(cmul(g[t][0], cconj(g[t][2])), (T)0.5));
     m12 = cadd(m12, cscale(cmul(g[t][1], cconj(g[t][2])), (T)0.5));
   }
+  const T r2 = (T)kInvSqrt2;
   C t3[3];
   if (mode == P_NODAL_IN) {
-    t3[0] = s[0]; t3[1] = s[1]; t3[2] = s[2];
+    t3[0] = col[0]; t3[1] = col[LD]; t3[2] = col[2 * LD];
   } else {
+    // t = B^H s: t_j = sum_t sum_a conj(g_ta) sigma_t,aj
     t3[0] = t3[1] = t3[2] = mkc<T>(0, 0);
-    const T r2 = (T)kInvSqrt2;
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
-      const C sxx = s[6 * t], syy = s[6 * t + 1], szz = s[6 * t + 2];
-      const C syz = cscale(s[6 * t + 3], r2), sxz = cscale(s[6 * t + 4], r2), sxy = cscale(s[6 * t + 5], r2);
+      const C* sp = col + 6 * t * LD;
+      const C sxx = sp[0], syy = sp[LD], szz = sp[2 * LD];
+      const C syz = cscale(sp[3 * LD], r2), sxz = cscale(sp[4 * LD], r2), sxy = cscale(sp[5 * LD], r2);
       t3[0] = cadd(t3[0], cadd(cadd(cjmul(g[t][0], sxx), cjmul(g[t][1], sxy)), cjmul(g[t][2], sxz)));
       t3[1] = cadd(t3[1], cadd(cadd(cjmul(g[t][0], sxy), cjmul(g[t][1], syy)), cjmul(g[t][2], syz)));
       t3[2] = cadd(t3[2], cadd(cadd(cjmul(g[t][0], sxz), cjmul(g[t][1], syz)), cjmul(g[t][2], szz)));
     }
   }
   // w = M^-1 t by the adjugate of the Hermitian matrix
-  // M = [[a, m01, m02], [conj m01, b, m12], [conj m02, conj m12, c]]
+  // M = [[A, m01, m02], [conj m01, B, m12], [conj m02, conj m12, Cc]]
   const T A = mdiag[0], B = mdiag[1], Cc = mdiag[2];
-  const C A00 = mkc<T>(B * Cc - cabs2(m12), 0);
-  const C A11 = mkc<T>(A * Cc - cabs2(m02), 0);
-  const C A22 = mkc<T>(A * B - cabs2(m01), 0);
-  // adj[0][1] = m02 conj(m12) - m01 c ; adj[0][2] = m01 m12 - m02 b ; adj[1][2] = m02 conj(m01) - a m12
+  const T A00 = B * Cc - cabs2(m12);
+  const T A11 = A * Cc - cabs2(m02);
+  const T A22 = A * B - cabs2(m01);
+  // adj[0][1] = m02 conj(m12) - m01 Cc ; adj[0][2] = m01 m12 - m02 B ; adj[1][2] = m02 conj(m01) - A m12
   const C A01 = csub(cmul(m02, cconj(m12)), cscale(m01, Cc));
   const C A02 = csub(cmul(m01, m12), cscale(m02, B));
   const C A12 = csub(cmul(m02, cconj(m01)), cscale(m12, A));
-  const T det = A * A00.x + (cmul(m01, cconj(A01))).x + (cmul(m02, cconj(A02))).x;
+  const T det = A * A00 + (cmul(m01, cconj(A01))).x + (cmul(m02, cconj(A02))).x;
   const T id = scale / det;
   C w[3];
-  w[0] = cscale(cadd(cadd(cscale(t3[0], A00.x), cmul(A01, t3[1])), cmul(A02, t3[2])), id);
-  w[1] = cscale(cadd(cadd(cjmul(A01, t3[0]), cscale(t3[1], A11.x)), cmul(A12, t3[2])), id);
-  w[2] = cscale(cadd(cadd(cjmul(A02, t3[0]), cjmul(A12, t3[1])), cscale(t3[2], A22.x)), id);
+  w[0] = cscale(cadd(cadd(cscale(t3[0], A00), cmul(A01, t3[1])), cmul(A02, t3[2])), id);
+  w[1] = cscale(cadd(cadd(cjmul(A01, t3[0]), cscale(t3[1], A11)), cmul(A12, t3[2])), id);
+  w[2] = cscale(cadd(cadd(cjmul(A02, t3[0]), cjmul(A12, t3[1])), cscale(t3[2], A22)), id);
   if (mode == P_NODAL_OUT) {
-    s[0] = w[0]; s[1] = w[1]; s[2] = w[2];
+    col[0] = w[0]; col[LD] = w[1]; col[2 * LD] = w[2];
     return;
   }
-  const T r2 = (T)kInvSqrt2;
+  // eps^ = B w: Mandel components of sym(g_t (x) w)
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
-    s[6 * t] = cmul(g[t][0], w[0]);
-    s[6 * t + 1] = cmul(g[t][1], w[1]);
-    s[6 * t + 2] = cmul(g[t][2], w[2]);
-    s[6 * t + 3] = cscale(cadd(cmul(g[t][1], w[2]), cmul(g[t][2], w[1])), r2);
-    s[6 * t + 4] = cscale(cadd(cmul(g[t][0], w[2]), cmul(g[t][2], w[0])), r2);
-    s[6 * t + 5] = cscale(cadd(cmul(g[t][0], w[1]), cmul(g[t][1], w[0])), r2);
+    C* sp = col + 6 * t * LD;
+    sp[0] = cmul(g[t][0], w[0]);
+    sp[LD] = cmul(g[t][1], w[1]);
+    sp[2 * LD] = cmul(g[t][2], w[2]);
+    sp[3 * LD] = cscale(cadd(cmul(g[t][1], w[2]), cmul(g[t][2], w[1])), r2);
+    sp[4 * LD] = cscale(cadd(cmul(g[t][0], w[2]), cmul(g[t][2], w[0])), r2);
+    sp[5 * LD] = cscale(cadd(cmul(g[t][0], w[1]), cmul(g[t][1], w[0])), r2);
   }
 }
 
@@ -258,8 +202,9 @@ template <typename T, int NZ, int NT>
 __global__ void __launch_bounds__(NT) pass_c_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 36;
+  constexpr int LD = FftSplit<NZ>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [M][NZ]
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [M][LD]
   const int kx = blockIdx.x, ky = blockIdx.y, l = blockIdx.z;
   const int ny = a.n[1], KX = a.kx;
   CgState* cg = a.cg + l;
@@ -271,120 +216,74 @@ __global__ void __launch_bounds__(NT) pass_c_3d(PassArgs<T> a) {
   const C* src = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
   for (int i = threadIdx.x; i < cin * NZ; i += NT) {
     const int c = i / NZ, z = i % NZ;
-    buf[c * NZ + z] = src[c * stride_c + z];
+    buf[c * LD + z] = src[c * stride_c + z];
   }
   __syncthreads();
-  if (cin == M) smem_fft<T, NZ, M, NZ, NT, -1>(buf, a.tw[2]);
-  else smem_fft<T, NZ, 3, NZ, NT, -1>(buf, a.tw[2]);
+  if (cin == M) smem_fft<T, NZ, M, LD, NT, -1>(buf, a.tw[2]);
+  else smem_fft<T, NZ, 3, LD, NT, -1>(buf, a.tw[2]);
   C e[3];
   e[0] = a.ph[0][kx];
   e[1] = a.ph[1][ky];
   for (int kz = threadIdx.x; kz < NZ; kz += NT) {
-    C s[M];
-#pragma unroll
-    for (int c = 0; c < M; ++c) s[c] = (c < cin) ? buf[c * NZ + kz] : mkc<T>(0, 0);
-    e[2] = a.ph[2][kz];
     if (kx == 0 && ky == 0 && kz == 0) {
-#pragma unroll
-      for (int c = 0; c < M; ++c) s[c] = mkc<T>(0, 0);
+      for (int c = 0; c < cout; ++c) buf[c * LD] = mkc<T>(0, 0);
     } else {
-      project_3d<T>(s, e, a.ih, a.inv_n, a.pmode);
+      e[2] = a.ph[2][kz];
+      project_3d<T, LD>(buf + kz, e, a.ih, a.inv_n, a.pmode);
     }
-#pragma unroll
-    for (int c = 0; c < M; ++c)
-      if (c < cout) buf[c * NZ + kz] = s[c];
   }
   __syncthreads();
-  if (cout == M) smem_fft<T, NZ, M, NZ, NT, +1>(buf, a.tw[2]);
-  else smem_fft<T, NZ, 3, NZ, NT, +1>(buf, a.tw[2]);
+  if (cout == M) smem_fft<T, NZ, M, LD, NT, +1>(buf, a.tw[2]);
+  else smem_fft<T, NZ, 3, LD, NT, +1>(buf, a.tw[2]);
   C* dst = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
   for (int i = threadIdx.x; i < cout * NZ; i += NT) {
     const int c = i / NZ, z = i % NZ;
-    dst[c * stride_c + z] = buf[c * NZ + z];
+    dst[c * stride_c + z] = buf[c * LD + z];
   }
 }
 
 // ---------------------------------------------------------------- pass E
-// grid (n_y/TY, n_z, L*Cc), Cc = m or D (nodal).
+// grid (n_y/TY, n_z, L*G): G = 6 tetrahedra (6 components each) or one group
+// of the 3 nodal components (E_NODAL); inverse real FFT along x and update.
 template <typename T, int NX, int TY, int NT>
 __global__ void __launch_bounds__(NT) pass_e_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
+  constexpr int GE = 6;
+  constexpr int LD = FftSplit<NX>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [NP][NX]
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [GE][NP][LD]
   __shared__ double red[NT / 32];
   __shared__ int flag;
-  const int Cc = (a.emode == E_NODAL) ? 3 : a.m;
-  const int l = blockIdx.z / Cc, c = blockIdx.z % Cc;
+  const bool nodal = (a.emode == E_NODAL);
+  const int G = nodal ? 1 : 6;
+  const int l = blockIdx.z / G, grp = blockIdx.z % G;
   const int z = blockIdx.y, y0 = blockIdx.x * TY;
   const int ny = a.n[1], nz = a.n[2];
   const int64_t N = a.N;
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
+  const int ge = nodal ? 3 : GE;
+  const int c0 = nodal ? 0 : grp * GE;
 
-  for (int i = threadIdx.x; i < KX * NP; i += NT) {
-    const int pr = i % NP, k = i / NP;
-    const C* src = a.spec + ((((int64_t)l * a.m + c) * KX + k) * nz + z) * ny + y0 + 2 * pr;
-    C xa = src[0], xb = src[1];
-    if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }
-    buf[pr * NX + k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);
-    if (k > 0 && k < NX / 2) buf[pr * NX + NX - k] = mkc<T>(xa.x + xb.y, xb.x - xa.y);
-  }
+  pass_e_unpack<T, NX, TY, NT, LD>(buf, a.spec + ((((int64_t)l * a.m + c0) * KX) * nz + z) * ny + y0, ge,
+                                   (int64_t)KX * nz * ny, (int64_t)nz * ny);
   __syncthreads();
-  smem_fft<T, NX, NP, NX, NT, +1>(buf, a.tw[0]);
-
-  T acc = 0;
+  smem_fft<T, NX, GE * NP, LD, NT, +1>(buf, a.tw[0]);
   const T alpha = (a.emode == E_CG) ? (T)cg->alpha : (T)0;
-  const int64_t base_v = ((int64_t)z * ny + y0) * NX;
-  for (int i = threadIdx.x; i < TY * NX; i += NT) {
-    const int yy = i / NX, xx = i % NX;
-    const int64_t v = base_v + i;
-    const T q = reinterpret_cast<const T*>(&buf[(yy / 2) * NX + xx])[yy & 1];
-    if (a.emode == E_NODAL) {
-      a.u64[((int64_t)l * 3 + c) * N + v] += (double)q;
-      continue;
-    }
-    const int64_t idx = ((int64_t)l * a.m + c) * N + v;
-    if (a.emode == E_CG) {
-      a.x[idx] += alpha * a.p[idx];
-      const T rv = a.r[idx] - alpha * q;
-      a.r[idx] = rv;
-      acc += rv * rv;
-    } else if (a.emode == E_INIT) {
-      const T rv = -q;
-      a.r[idx] = rv;
-      a.x[idx] = 0;
-      acc += rv * rv;
-    } else {
-      a.out[idx] = q;
-    }
-  }
+  const T acc = pass_e_update<T, NX, TY, NT, LD>(a, buf, ge, ((int64_t)z * ny + y0) * NX,
+                                                 ((int64_t)l * a.m + c0) * N, (int64_t)l * 3 * N, alpha);
 
   if (a.emode == E_CG || a.emode == E_INIT) {
     const double s = block_sum<NT>((double)acc, red);
-    const int nblk = gridDim.x * gridDim.y * Cc;
-    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * c);
+    const int nblk = gridDim.x * gridDim.y * G;
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * grp);
     double* part = a.part + (int64_t)l * a.part_stride;
     if (publish_partial(s, part, &cg->cnt_e, blk, nblk, &flag)) {
       const double rr = sum_partials<NT>(part, nblk, red);
-      if (threadIdx.x == 0) {
-        if (a.emode == E_INIT) {
-          cg->rr0 = rr; cg->rr = rr; cg->it = 0; cg->beta = 0.0;
-          cg->status = !isfinite(rr) ? ST_BAD : (rr == 0.0 ? ST_CONV : ST_RUN);
-        } else {
-          cg->it += 1;
-          if (!isfinite(rr)) { cg->status = ST_BAD; }
-          else {
-            cg->beta = rr / cg->rr;
-            cg->rr = rr;
-            if (rr <= cg->tol2 * cg->rr0) cg->status = ST_CONV;
-            else if (cg->it >= cg->maxit) cg->status = ST_MAXIT;
-          }
-        }
-        cg->cnt_e = 0;
-      }
+      if (threadIdx.x == 0) finish_rr(cg, rr, a.emode == E_INIT);
     }
   }
 }
@@ -396,8 +295,9 @@ template <> struct Tile3D<double> { static constexpr int TY = 4; static constexp
 
 template <typename T, int NX>
 cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile3D<T>::TY, NT = 256;
-  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * NX;
+  constexpr int TY = Tile3D<T>::TY;
+  constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
+  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_3d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
@@ -407,19 +307,21 @@ cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
 }
 template <typename T, int NX>
 cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile3D<T>::TY, NT = 256;
-  const size_t sm = sizeof(cplx<T>) * (TY / 2) * NX;
+  constexpr int TY = Tile3D<T>::TY;
+  constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
+  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_3d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.emode == E_NODAL ? 3 : a.m));
+  dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.emode == E_NODAL ? 1 : 6));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
 template <typename T, int NY, bool FWD>
 cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TZB = Tile3D<T>::TZB, NT = 256;
-  const size_t sm = sizeof(cplx<T>) * TZB * NY;
+  constexpr int TZB = Tile3D<T>::TZB;
+  constexpr int NT = fft_threads<NY, TZB>();
+  const size_t sm = sizeof(cplx<T>) * TZB * FftSplit<NY>::LD;
   auto k = pass_y_3d<T, NY, TZB, NT, FWD>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
@@ -436,8 +338,8 @@ template <typename T, int NY> cudaError_t launch_yb_3d_n(const PassArgs<T>& a, c
 }
 template <typename T, int NZ>
 cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int NT = (sizeof(T) == 8 || NZ >= 256) ? 512 : 256;
-  const size_t sm = sizeof(cplx<T>) * 36 * NZ;
+  constexpr int NT = fft_threads<NZ, 36>();
+  const size_t sm = sizeof(cplx<T>) * 36 * FftSplit<NZ>::LD;
   auto k = pass_c_3d<T, NZ, NT>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }

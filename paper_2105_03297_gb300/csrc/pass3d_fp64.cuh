@@ -58,6 +58,7 @@ constexpr int kRVox = (kRTX + 1) * (kRTY + 1) * (kRTZ + 1);
 __global__ void __launch_bounds__(256) residual_3d(Fp64Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* contrib = reinterpret_cast<double*>(smem_raw);  // [kRVox][8][3]
+  double* cabs = contrib + kRVox * 24;                    // [kRVox][8][3] magnitudes
   __shared__ double red[8];
   __shared__ int flag;
   const int nzt = a.n[2] / kRTZ;
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(256) residual_3d(Fp64Args a) {
     double eps[6][6];
     strain_3d(u, a.N, a.n, vx, vy, vz, em, a.ih, eps);
     const double e = a.E[((int64_t)vz * a.n[1] + vy) * a.n[0] + vx];
-    double f[8][3];
+    double f[8][3], fa[8][3];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) f[c][0] = f[c][1] = f[c][2] = 0.0;
+    for (int c = 0; c < 8; ++c) f[c][0] = f[c][1] = f[c][2] = fa[c][0] = fa[c][1] = fa[c][2] = 0.0;
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       double s[6];
@@ -96,23 +97,33 @@ __global__ void __launch_bounds__(256) residual_3d(Fp64Args a) {
         f[v1][j] += Pa - Pb;
         f[v2][j] += Pb - Pc;
         f[7][j] += Pc;
+        fa[0][j] += fabs(Pa);
+        fa[v1][j] += fabs(Pa) + fabs(Pb);
+        fa[v2][j] += fabs(Pb) + fabs(Pc);
+        fa[7][j] += fabs(Pc);
       }
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) contrib[(i * 8 + c) * 3 + j] = f[c][j];
+      for (int j = 0; j < 3; ++j) {
+        contrib[(i * 8 + c) * 3 + j] = f[c][j];
+        cabs[(i * 8 + c) * 3 + j] = fa[c][j];
+      }
   }
   __syncthreads();
   const int lx = threadIdx.x % kRTX, ly = (threadIdx.x / kRTX) % kRTY, lz = threadIdx.x / (kRTX * kRTY);
-  double fn[3] = {0, 0, 0};
+  double fn[3] = {0, 0, 0}, fna[3] = {0, 0, 0};
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
     const int ex = lx + 1 - dx, ey = ly + 1 - dy, ez = lz + 1 - dz;
     const int i = (ez * (kRTY + 1) + ey) * (kRTX + 1) + ex;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) fn[j] += contrib[(i * 8 + c) * 3 + j];
+    for (int j = 0; j < 3; ++j) {
+      fn[j] += contrib[(i * 8 + c) * 3 + j];
+      fna[j] += cabs[(i * 8 + c) * 3 + j];
+    }
   }
   const int64_t node = ((int64_t)(z0 + lz) * a.n[1] + (y0 + ly)) * a.n[0] + x0 + lx;
   if (a.fout_f32) {
@@ -125,18 +136,23 @@ __global__ void __launch_bounds__(256) residual_3d(Fp64Args a) {
     for (int j = 0; j < 3; ++j) fo[j * a.N + node] = fn[j];
   }
   const double acc = fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2];
+  const double acca = fna[0] * fna[0] + fna[1] * fna[1] + fna[2] * fna[2];
   const double s = block_sum<256>(acc, red);
+  const double sa = block_sum<256>(acca, red);
   const int nblk = gridDim.x * gridDim.y * nzt;
   const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * tz);
   double* part = a.part + (int64_t)l * a.part_stride;
+  double* parta = part + a.part_stride / 2;
+  if (threadIdx.x == 0) parta[blk] = sa;
   if (publish_partial(s, part, &cg->cnt_r, blk, nblk, &flag)) {
     const double t = sum_partials<256>(part, nblk, red);
-    if (threadIdx.x == 0) { cg->fn2 = t; cg->cnt_r = 0; }
+    const double ta = sum_partials<256>(parta, nblk, red);
+    if (threadIdx.x == 0) { cg->fn2 = t; cg->fa2 = ta; cg->cnt_r = 0; }
   }
 }
 
 inline cudaError_t launch_residual_3d(const Fp64Args& a, cudaStream_t s) {
-  const size_t sm = sizeof(double) * kRVox * 24;
+  const size_t sm = sizeof(double) * kRVox * 48;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(residual_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
   dim3 grid(a.n[0] / kRTX, a.n[1] / kRTY, (a.n[2] / kRTZ) * a.L);

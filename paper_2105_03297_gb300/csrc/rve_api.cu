@@ -294,7 +294,7 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
   const double inner_tol = mixed ? std::fmax(rel_tol, 2e-5) : rel_tol;
   const int max_outer = mixed ? 12 : 6;
   std::vector<double> f0(L, 0.0), frel(L, 0.0), cgrel(L, 0.0);
-  std::vector<int> iters(L, 0), steps(L, 0), bad(L, 0), active(L, 1);
+  std::vector<int> iters(L, 0), steps(L, 0), bad(L, 0), active(L, 1), floor_hit(L, 0);
   std::memset(h->cg_h, 0, (size_t)L * sizeof(CgState));
   for (int l = 0; l < L; ++l) { h->cg_h[l].active = 1; h->cg_h[l].status = ST_RUN; }
   int rc = write_state(h, L);
@@ -316,10 +316,20 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
       if (!std::isfinite(fn2)) { bad[l] = 1; active[l] = 0; continue; }
       const double prev = frel[l];
       frel[l] = (f0[l] > 0.0) ? std::sqrt(fn2) / f0[l] : 0.0;
-      // stop: tolerance met, step or iteration budget spent, or no progress
-      // (round-off floor of the FP64 residual)
+      // Round-off level of f: a bound on the rounding error of summing the
+      // terms of every nodal force in FP64 (backward-error floor).  A load
+      // case whose residual is below it is solved, even if f_0 itself is at
+      // that level (the macroscopic strain is already an equilibrium state).
+      const double floor_abs = 64.0 * 2.220446049250313e-16 * std::sqrt(h->cg_h[l].fa2);
+      const bool at_floor = std::sqrt(fn2) <= floor_abs;
+      if (at_floor) floor_hit[l] = 1;
+      // stop: tolerance met, at the round-off floor, step or iteration budget
+      // spent, or no progress
       const bool stalled = step >= 2 && frel[l] > 0.5 * prev;
-      if (frel[l] <= rel_tol || step >= max_outer || iters[l] >= max_iter || stalled) { active[l] = 0; continue; }
+      if (frel[l] <= rel_tol || at_floor || step >= max_outer || iters[l] >= max_iter || stalled) {
+        active[l] = 0;
+        continue;
+      }
       any = true;
     }
     if (!any) break;
@@ -366,7 +376,7 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
   for (int l = 0; l < L; ++l) {
     int st = RVE_OK;
     if (bad[l]) st = RVE_ERR_NONFINITE;
-    else if (frel[l] > rel_tol) st = RVE_ERR_NOT_CONVERGED;
+    else if (frel[l] > rel_tol && !floor_hit[l]) st = RVE_ERR_NOT_CONVERGED;
     if (info) {
       info[l].iterations = iters[l];
       info[l].refine_steps = steps[l];

@@ -38,107 +38,175 @@ template <typename C> __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x
 struct CgState {
   double rr, rr0, pq, alpha, beta, tol2;
   double fn2;        // squared FP64 nodal residual norm (last residual pass)
+  double fa2;        // squared norm of the summed magnitudes of the terms of f (round-off scale)
   int it, maxit, status, active;  // active: the outer refinement still runs this load case
   unsigned cnt_a, cnt_e, cnt_r, pad;
 };
 
 enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BAD = 3 };
 
-// ------------------------------------------------------- Stockham FFT
+// ------------------------------------------------------- FFT in shared memory
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-// R-point DFT of v in place, sign S (-1 forward, +1 inverse).
-template <int S, int R, typename C> __device__ __forceinline__ void dft_small(C* v) {
+// cos(2 pi j / 32) for j = 0..8 (first quadrant, FP64 values of the
+// mathematical constants); the other twiddles of the register FFTs follow by
+// symmetry.
+__host__ __device__ constexpr double kCos32q(int j) {
+  return j == 0 ? 1.0 : j == 1 ? 0.98078528040323044913 : j == 2 ? 0.92387953251128675613
+       : j == 3 ? 0.83146961230254523708 : j == 4 ? 0.70710678118654752440 : j == 5 ? 0.55557023301960222474
+       : j == 6 ? 0.38268343236508977173 : j == 7 ? 0.19509032201612826785 : 0.0;
+}
+__host__ __device__ constexpr double kCos32(int j) {
+  return j <= 8 ? kCos32q(j) : j <= 16 ? -kCos32q(16 - j) : j <= 24 ? -kCos32q(j - 16) : kCos32q(32 - j);
+}
+__host__ __device__ constexpr double kSin32(int j) { return kCos32((j + 24) & 31); }
+
+// In-register FFT of R = 1, 2, 4, 8, 16 or 32 points (natural order in and
+// out), sign S: exp(S 2 pi i n k / R).  Radix-2 decimation in time, unrolled.
+template <int R, int S, typename C>
+__device__ __forceinline__ void fft_reg(C* v) {
+  using T = decltype(v[0].x);
   if constexpr (R == 2) {
-    C a = v[0], b = v[1];
+    const C a = v[0], b = v[1];
     v[0] = cadd(a, b); v[1] = csub(a, b);
   } else if constexpr (R == 4) {
-    C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-    C a2 = cadd(v[1], v[3]), a3 = cmul_i<S>(csub(v[1], v[3]));
+    const C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    const C a2 = cadd(v[1], v[3]), a3 = cmul_i<S>(csub(v[1], v[3]));
     v[0] = cadd(a0, a2); v[2] = csub(a0, a2);
     v[1] = cadd(a1, a3); v[3] = csub(a1, a3);
-  } else if constexpr (R == 8) {
-    using T = decltype(v[0].x);
-    const T h = (T)0.70710678118654752440;
-    // two radix-4 on even/odd, then combine with W8^r
-    C e[4] = {v[0], v[2], v[4], v[6]};
-    C o[4] = {v[1], v[3], v[5], v[7]};
-    dft_small<S, 4>(e);
-    dft_small<S, 4>(o);
-    // o[r] *= exp(S*2*pi*i*r/8)
-    C o1; o1.x = h * (o[1].x - (T)S * o[1].y); o1.y = h * (o[1].y + (T)S * o[1].x);
-    C o2 = cmul_i<S>(o[2]);
-    C o3; o3.x = h * (-o[3].x - (T)S * o[3].y); o3.y = h * (-o[3].y + (T)S * o[3].x);
-    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
-    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
-  }
-}
-
-// One Stockham autosort stage of radix R with NS = product of the previous
-// radices, over NB transforms of length N stored at buf + b*LD.  Values are
-// staged in registers so the stage is in place; two barriers per stage.
-// tw[t] = exp(-2 pi i t / N) (host FP64 libm, rounded to T).
-template <typename T, int N, int NB, int LD, int NT, int S, int R, int NS>
-__device__ __forceinline__ void stockham_stage(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int NBF = NB * (N / R);
-  constexpr int PER = (NBF + NT - 1) / NT;
-  C v[PER][R];
+  } else if constexpr (R > 4) {
+    C e[R / 2], o[R / 2];
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int f = threadIdx.x + i * NT;
-    if ((NBF % NT) == 0 || f < NBF) {
-      const int b = f / (N / R), j = f % (N / R);
-      const C* src = buf + b * LD + j;
+    for (int i = 0; i < R / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+    fft_reg<R / 2, S>(e);
+    fft_reg<R / 2, S>(o);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = src[r * (N / R)];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int f = threadIdx.x + i * NT;
-    if ((NBF % NT) == 0 || f < NBF) {
-      const int b = f / (N / R), j = f % (N / R);
-      const int k = j % NS;
-      if constexpr (NS > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C w = __ldg(tw + r * k * (N / (NS * R)));
-          if (S > 0) w.y = -w.y;
-          v[i][r] = cmul(v[i][r], w);
-        }
+    for (int k = 0; k < R / 2; ++k) {
+      C t = o[k];
+      if (k != 0) {
+        const int j = k * (32 / R);
+        C w;
+        w.x = (T)kCos32(j);
+        w.y = (T)(S * kSin32(j));
+        t = cmul(o[k], w);
       }
-      dft_small<S, R>(v[i]);
-      C* dst = buf + b * LD + (j / NS) * NS * R + k;
-#pragma unroll
-      for (int q = 0; q < R; ++q) dst[q * NS] = v[i][q];
+      v[k] = cadd(e[k], t);
+      v[k + R / 2] = csub(e[k], t);
     }
   }
-  __syncthreads();
 }
 
-template <typename T, int N, int NB, int LD, int NT, int S, int NS>
-__device__ __forceinline__ void stockham_from(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  if constexpr (NS * 8 <= N && (ilog2c(N / NS) % 3) == 0) {
-    stockham_stage<T, N, NB, LD, NT, S, 8, NS>(buf, tw);
-    stockham_from<T, N, NB, LD, NT, S, NS * 8>(buf, tw);
-  } else if constexpr (NS * 4 <= N) {
-    stockham_stage<T, N, NB, LD, NT, S, 4, NS>(buf, tw);
-    stockham_from<T, N, NB, LD, NT, S, NS * 4>(buf, tw);
-  } else if constexpr (NS * 2 <= N) {
-    stockham_stage<T, N, NB, LD, NT, S, 2, NS>(buf, tw);
-  }
+// Four-step split N = N1 * N2 with N1 <= N2 <= 32.
+template <int N> struct FftSplit {
+  static constexpr int N1 = (N <= 16) ? 4 : (N == 32) ? 4 : (N == 64) ? 8 : (N == 128) ? 8
+                          : (N == 256) ? 16 : (N == 512) ? 16 : 32;
+  static constexpr int N2 = N / N1;
+  // leading dimension of one transform in shared memory (room for the padded
+  // transpose of the middle step)
+  static constexpr int LD = N + N2;
+};
+
+// Threads that give one work item per thread in both steps for NB transforms,
+// within [128, 1024], a multiple of 32.
+template <int N, int NB> constexpr int fft_threads() {
+  constexpr int w = NB * FftSplit<N>::N2;
+  constexpr int t = w < 128 ? 128 : (w > 1024 ? 1024 : w);
+  return (t + 31) / 32 * 32;
 }
 
-// Batched in-place FFT (unnormalised) of NB transforms of length N in shared
-// memory.  Caller must __syncthreads() before (data written) — the function
-// ends with a barrier.
+// Batched in-place FFT (unnormalised, sign S) of NB transforms of length N
+// stored at buf + b*LD, natural order in and out.
+//   step 1: for every (b, n1): FFT over n2 of x[n1 + N1 n2] in registers,
+//           twiddle by exp(S 2 pi i n1 k2 / N), store transposed with a padded
+//           stride (N1 + 1) so that both access patterns are conflict-free;
+//   step 2: for every (b, k2): FFT over n1 in registers, store X[k2 + N2 k1].
+// tw[t] = exp(-2 pi i t / N) (host FP64 libm, rounded to T).  The caller must
+// __syncthreads() before; the function ends with a barrier.
 template <typename T, int N, int NB, int LD, int NT, int S>
 __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  stockham_from<T, N, NB, LD, NT, S, 1>(buf, tw);
+  using C = cplx<T>;
+  constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
+  static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
+  constexpr int W1 = NB * N1, W2 = NB * N2;
+  constexpr int I1 = (W1 + NT - 1) / NT, I2 = (W2 + NT - 1) / NT;
+  {
+    C v[I1][N2];
+#pragma unroll
+    for (int i = 0; i < I1; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W1 % NT) == 0 || it < W1) {
+        const int b = it / N1, n1 = it % N1;
+        const C* src = buf + b * LD + n1;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v[i][n2] = src[n2 * N1];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < I1; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W1 % NT) == 0 || it < W1) {
+        const int b = it / N1, n1 = it % N1;
+        fft_reg<N2, S>(v[i]);
+        C* dst = buf + b * LD + n1;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          C t = v[i][k2];
+          if (k2 > 0 && n1 > 0) {
+            C w = __ldg(tw + n1 * k2);
+            if (S > 0) w.y = -w.y;
+            t = cmul(t, w);
+          }
+          dst[k2 * (N1 + 1)] = t;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    C v[I2][N1];
+#pragma unroll
+    for (int i = 0; i < I2; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W2 % NT) == 0 || it < W2) {
+        const int b = it / N2, k2 = it % N2;
+        const C* src = buf + b * LD + k2 * (N1 + 1);
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[i][n1] = src[n1];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < I2; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W2 % NT) == 0 || it < W2) {
+        const int b = it / N2, k2 = it % N2;
+        fft_reg<N1, S>(v[i]);
+        C* dst = buf + b * LD + k2;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) dst[k1 * N2] = v[i][k1];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// 16-byte vector of T (4 floats or 2 doubles) for the streaming loops.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using t = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using t = double2; static constexpr int n = 2; };
+template <typename T> __device__ __forceinline__ void vload(T* d, const T* s) {
+  const typename Vec16<T>::t w = *reinterpret_cast<const typename Vec16<T>::t*>(s);
+  const T* a = reinterpret_cast<const T*>(&w);
+#pragma unroll
+  for (int i = 0; i < Vec16<T>::n; ++i) d[i] = a[i];
+}
+template <typename T> __device__ __forceinline__ void vstore(T* d, const T* s) {
+  typename Vec16<T>::t w;
+  T* a = reinterpret_cast<T*>(&w);
+#pragma unroll
+  for (int i = 0; i < Vec16<T>::n; ++i) a[i] = s[i];
+  *reinterpret_cast<typename Vec16<T>::t*>(d) = w;
 }
 
 // ------------------------------------------------------------ reductions
