@@ -32,6 +32,7 @@ WORKLOADS = {
     "gauss1024_fp64": ("gauss1024", "fp64", 1e-11),
     "lognormal64": ("lognormal64", "mixed", 1e-11),
     "spheres128": ("spheres128", "mixed", 1e-11),
+    "lognormal128": ("lognormal128", "mixed", 1e-10),
     "lognormal256": ("lognormal256", "mixed", 1e-10),
     "lognormal256_fp64": ("lognormal256", "fp64", 1e-10),
 }

@@ -178,6 +178,10 @@ def config_inputs(name):
         n = (64, 64, 64)
         return dict(n=n, E=lognormal_field(n, 0.0, 1.0, seed=1005), nu=0.3,
                     E_macro=unit_load_cases(3))
+    if name == "lognormal128":    # 3D 128^3 log-normal, one load case (profiling size)
+        n = (128, 128, 128)
+        return dict(n=n, E=lognormal_field(n, 0.0, 1.0, seed=1007), nu=0.3,
+                    E_macro=unit_load_cases(3)[:1])
     if name == "lognormal256":    # 3D 256^3 log-normal, one load case (throughput)
         n = (256, 256, 256)
         return dict(n=n, E=lognormal_field(n, 0.0, 1.0, seed=1006), nu=0.3,

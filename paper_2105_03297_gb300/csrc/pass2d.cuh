@@ -44,101 +44,107 @@ __device__ __forceinline__ void finish_rr(CgState* cg, double rr, bool init) {
 
 // ------------------------------------------------------------------------
 // Pass A body, shared by 2D (GS = 3 components per element) and 3D (GS = 6):
-// stream TY rows of NX voxels starting at voxel v0 (16-byte vectors, two
-// groups of loads in flight per thread), apply the material, and write the
-// stress of component j into buf[(j*NP + yy/2)*LD + x] (real part for even
-// row yy, imaginary for odd).  Returns this thread's share of <p, C p>.
-template <typename T, int NX, int TY, int GS, int NT, int LD>
+// stream TY rows of NX voxels starting at voxel v0, apply the material, and
+// pack the stress of component j, rows (2 pr, 2 pr + 1), as one complex row
+// buf[(j*NP + pr)*LD + x] = sigma(2 pr, x) + i sigma(2 pr + 1, x).  A thread
+// handles a unit of two rows x VL columns (16-byte loads of both rows of every
+// component in flight together; 2-complex stores to shared memory).  Returns
+// this thread's share of <p, C p>.
+template <typename T, int NX, int TY, int GS, int NT, int LD, int VL = Vec16<T>::n>
 __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int l, int c0, int64_t v0,
                                          bool nodal, T beta, bool use_old) {
-  constexpr int VL = Vec16<T>::n;
-  constexpr int NV = TY * NX / VL;
+  using C = cplx<T>;
   constexpr int NP = TY / 2;
-  constexpr int U = 2;
+  constexpr int NU = NP * (NX / VL);
+  static_assert(LD % 2 == 0, "row starts must stay 16-byte aligned");
+  static_assert(VL % 2 == 0, "units pair complex values");
   const int64_t N = a.N;
   T acc = 0;
-  for (int base = 0; base < NV; base += U * NT) {
-    T pv[U][GS][VL];
-    T ev[U][VL];
+  for (int i = threadIdx.x; i < NU; i += NT) {
+    const int pr = i / (NX / VL), x0 = (i % (NX / VL)) * VL;
+    const int64_t va = v0 + (int64_t)(2 * pr) * NX + x0;
+    T pv[2][GS][VL];
+    T ev[2][VL];
+    if (nodal) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * NT + threadIdx.x;
-      if (i < NV) {
-        const int64_t v = v0 + (int64_t)i * VL;
-        if (nodal) {
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j) {
-            if (j < a.dim) vload(pv[u][j], a.in + ((int64_t)l * a.dim + j) * N + v);
-            else {
+        for (int j = 0; j < GS; ++j) {
+          if (j < a.dim) vloadn<T, VL>(pv[h][j], a.in + ((int64_t)l * a.dim + j) * N + va + h * NX);
+          else {
 #pragma unroll
-              for (int q = 0; q < VL; ++q) pv[u][j][q] = 0;
-            }
+            for (int q = 0; q < VL; ++q) pv[h][j][q] = 0;
           }
-        } else {
-          if (a.amode != A_BARE) vload(ev[u], a.E + v);
+        }
+    } else {
 #pragma unroll
-          for (int j = 0; j < GS; ++j) {
-            const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + v;
-            if (a.amode == A_CG) {
-              vload(pv[u][j], a.r + idx);
-              if (use_old) {
-                T po[VL];
-                vload(po, a.p + idx);
+      for (int h = 0; h < 2; ++h) {
+        if (a.amode != A_BARE) vloadn<T, VL>(ev[h], a.E + va + h * NX);
 #pragma unroll
-                for (int q = 0; q < VL; ++q) pv[u][j][q] += beta * po[q];
-              }
-            } else if (a.amode == A_MACRO) {
+        for (int j = 0; j < GS; ++j) {
+          const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + va + h * NX;
+          if (a.amode == A_CG) {
+            vloadn<T, VL>(pv[h][j], a.r + idx);
+          } else if (a.amode == A_MACRO) {
 #pragma unroll
-              for (int q = 0; q < VL; ++q) pv[u][j][q] = (T)a.emac[l * GS + j];
-            } else {
-              vload(pv[u][j], a.in + idx);
-            }
+            for (int q = 0; q < VL; ++q) pv[h][j][q] = (T)a.emac[l * GS + j];
+          } else {
+            vloadn<T, VL>(pv[h][j], a.in + idx);
           }
         }
       }
-    }
+      if (a.amode == A_CG && use_old) {
+        T po[2][GS][VL];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * NT + threadIdx.x;
-      if (i < NV) {
-        const int e0 = i * VL;  // element offset inside the tile
-        const int yy = e0 / NX, x0 = e0 % NX;
-        if (!nodal && a.amode == A_CG) {
-          const int64_t v = v0 + (int64_t)e0;
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j) vstore(a.p + ((int64_t)l * a.m + c0 + j) * N + v, pv[u][j]);
-        }
+          for (int j = 0; j < GS; ++j) vloadn<T, VL>(po[h][j], a.p + ((int64_t)l * a.m + c0 + j) * N + va + h * NX);
 #pragma unroll
-        for (int q = 0; q < VL; ++q) {
-          T s[GS];
-          if (nodal || a.amode == A_BARE) {
-#pragma unroll
-            for (int j = 0; j < GS; ++j) s[j] = pv[u][j][q];
-          } else {
-            // isotropic material, unit-modulus Lame constants times E_v
-            T p1[GS];
-#pragma unroll
-            for (int j = 0; j < GS; ++j) p1[j] = pv[u][j][q];
-            constexpr int D = (GS == 3) ? 2 : 3;
-            T tr = 0;
-#pragma unroll
-            for (int j = 0; j < D; ++j) tr += p1[j];
-            tr *= a.lam;
-            const T e = ev[u][q];
-#pragma unroll
-            for (int j = 0; j < D; ++j) s[j] = e * (tr + a.mu2 * p1[j]);
-#pragma unroll
-            for (int j = D; j < GS; ++j) s[j] = e * (a.mu2 * p1[j]);
-            if (a.amode == A_CG) {
-#pragma unroll
-              for (int j = 0; j < GS; ++j) acc += p1[j] * s[j];
-            }
-          }
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int j = 0; j < GS; ++j)
-            reinterpret_cast<T*>(&buf[(j * NP + yy / 2) * LD + x0 + q])[yy & 1] = s[j];
+#pragma unroll
+            for (int q = 0; q < VL; ++q) pv[h][j][q] += beta * po[h][j][q];
+      }
+      if (a.amode == A_CG) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < GS; ++j) vstoren<T, VL>(a.p + ((int64_t)l * a.m + c0 + j) * N + va + h * NX, pv[h][j]);
+      }
+    }
+    T sv[2][GS][VL];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < VL; ++q) {
+        if (nodal || a.amode == A_BARE) {
+#pragma unroll
+          for (int j = 0; j < GS; ++j) sv[h][j][q] = pv[h][j][q];
+        } else {
+          // isotropic material, unit-modulus Lame constants times E_v
+          constexpr int D = (GS == 3) ? 2 : 3;
+          T tr = 0;
+#pragma unroll
+          for (int j = 0; j < D; ++j) tr += pv[h][j][q];
+          tr *= a.lam;
+          const T e = ev[h][q];
+#pragma unroll
+          for (int j = 0; j < D; ++j) sv[h][j][q] = e * (tr + a.mu2 * pv[h][j][q]);
+#pragma unroll
+          for (int j = D; j < GS; ++j) sv[h][j][q] = e * (a.mu2 * pv[h][j][q]);
+          if (a.amode == A_CG) {
+#pragma unroll
+            for (int j = 0; j < GS; ++j) acc += pv[h][j][q] * sv[h][j][q];
+          }
         }
       }
+#pragma unroll
+    for (int j = 0; j < GS; ++j) {
+      C* dst = buf + (j * NP + pr) * LD + x0;
+#pragma unroll
+      for (int q = 0; q < VL; q += 2)
+        cstore2<T>(dst + q, mkc<T>(sv[0][j][q], sv[1][j][q]), mkc<T>(sv[0][j][q + 1], sv[1][j][q + 1]));
     }
   }
   return acc;
@@ -161,9 +167,7 @@ __device__ __forceinline__ void pass_a_store(const cplx<T>* buf, int gs, cplx<T>
     const C xa = cscale(cadd(A, Bc), (T)0.5);
     const C d = csub(A, Bc);
     const C xb = mkc<T>((T)0.5 * d.y, (T)-0.5 * d.x);
-    C* dst = base + j * comp_stride + (int64_t)k * k_stride + 2 * pr;
-    dst[0] = xa;
-    dst[1] = xb;
+    cstore2<T>(base + j * comp_stride + (int64_t)k * k_stride + 2 * pr, xa, xb);
   }
 }
 
@@ -171,7 +175,7 @@ __device__ __forceinline__ void pass_a_store(const cplx<T>* buf, int gs, cplx<T>
 // grid (n_y/TY, groups, L), groups = n_q element blocks (n_s components each)
 // or one block of D nodal components (A_NODAL).
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT) pass_a_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_a_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 3;
@@ -264,7 +268,7 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
 
 // grid (n_x/2+1, L); one k_x column of all six spectra per block.
 template <typename T, int NY, int NT>
-__global__ void __launch_bounds__(NT) pass_c_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 6;
   constexpr int LD = FftSplit<NY>::LD;
@@ -278,9 +282,26 @@ __global__ void __launch_bounds__(NT) pass_c_2d(PassArgs<T> a) {
   const int cin = (a.pmode == P_NODAL_IN) ? 2 : M;
   const int cout = (a.pmode == P_NODAL_OUT) ? 2 : M;
   const C* src = a.spec + (((int64_t)l * M) * KX + kx) * NY;
-  for (int i = threadIdx.x; i < cin * NY; i += NT) {
-    const int c = i / NY, y = i % NY;
-    buf[c * LD + y] = src[(int64_t)c * KX * NY + y];
+  {
+    // batched 2-complex loads: all of a thread's loads are in flight together
+    constexpr int PER = (M * NY / 2 + NT - 1) / NT;
+    C v[PER][2];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < cin * NY / 2) {
+        const int c = i / (NY / 2), y = 2 * (i % (NY / 2));
+        cload2<T>(v[k], src + (int64_t)c * KX * NY + y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < cin * NY / 2) {
+        const int c = i / (NY / 2), y = 2 * (i % (NY / 2));
+        cstore2<T>(buf + c * LD + y, v[k][0], v[k][1]);
+      }
+    }
   }
   __syncthreads();
   if (cin == M) smem_fft<T, NY, M, LD, NT, -1>(buf, a.tw[1]);
@@ -305,9 +326,11 @@ __global__ void __launch_bounds__(NT) pass_c_2d(PassArgs<T> a) {
   if (cout == M) smem_fft<T, NY, M, LD, NT, +1>(buf, a.tw[1]);
   else smem_fft<T, NY, 2, LD, NT, +1>(buf, a.tw[1]);
   C* dst = a.spec + (((int64_t)l * M) * KX + kx) * NY;
-  for (int i = threadIdx.x; i < cout * NY; i += NT) {
-    const int c = i / NY, y = i % NY;
-    dst[(int64_t)c * KX * NY + y] = buf[c * LD + y];
+  for (int i = threadIdx.x; i < cout * NY / 2; i += NT) {
+    const int c = i / (NY / 2), y = 2 * (i % (NY / 2));
+    C v[2];
+    cload2<T>(v, buf + c * LD + y);
+    cstore2<T>(dst + (int64_t)c * KX * NY + y, v[0], v[1]);
   }
 }
 
@@ -323,8 +346,9 @@ __device__ __forceinline__ void pass_e_unpack(cplx<T>* buf, const cplx<T>* src, 
   constexpr int KX = NX / 2 + 1;
   for (int i = threadIdx.x; i < ge * KX * NP; i += NT) {
     const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
-    const C* s = src + j * comp_stride + (int64_t)k * k_stride + 2 * pr;
-    C xa = s[0], xb = s[1];
+    C ab[2];
+    cload2<T>(ab, src + j * comp_stride + (int64_t)k * k_stride + 2 * pr);
+    C xa = ab[0], xb = ab[1];
     if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }  // C2R ignores these imaginary parts
     C* row = buf + (j * NP + pr) * LD;
     row[k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);                                  // X_a + i X_b
@@ -333,68 +357,74 @@ __device__ __forceinline__ void pass_e_unpack(cplx<T>* buf, const cplx<T>* src, 
 }
 
 // Per-voxel update of ge components over the tile of TY rows starting at
-// voxel v0; q of component j comes from the packed rows j*NP...  idx0 /
-// uidx0: offsets of the first component's [N] slab in the CG vectors / the
-// FP64 nodal field (components follow at stride N).  Returns the thread's
-// share of <r, r>.
+// voxel v0; q of component j, rows (2 pr, 2 pr + 1), is the real / imaginary
+// part of the packed row j*NP + pr.  A thread handles two rows x VL columns of
+// one component.  idx0 / uidx0: offsets of the first component's [N] slab in
+// the CG vectors / the FP64 nodal field (components follow at stride N).
+// Returns the thread's share of <r, r>.
 template <typename T, int NX, int TY, int NT, int LD>
 __device__ __forceinline__ T pass_e_update(const PassArgs<T>& a, const cplx<T>* buf, int ge, int64_t v0,
                                            int64_t idx0, int64_t uidx0, T alpha) {
+  using C = cplx<T>;
   constexpr int VL = Vec16<T>::n;
-  constexpr int NV = TY * NX / VL;
   constexpr int NP = TY / 2;
-  constexpr int U = 2;
+  constexpr int NU = NP * (NX / VL);
+  static_assert(LD % 2 == 0, "row starts must stay 16-byte aligned");
   T acc = 0;
-  for (int base = 0; base < ge * NV; base += U * NT) {
-    T q[U][VL], xv[U][VL], rv[U][VL], pv[U][VL];
+  for (int i = threadIdx.x; i < ge * NU; i += NT) {
+    const int j = i / NU, iu = i % NU;
+    const int pr = iu / (NX / VL), x0 = (iu % (NX / VL)) * VL;
+    T q[2][VL];
+    const C* src = buf + (j * NP + pr) * LD + x0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * NT + threadIdx.x;
-      if (i < ge * NV) {
-        const int j = i / NV, e0 = (i % NV) * VL;
-        const int yy = e0 / NX, x0 = e0 % NX;
-#pragma unroll
-        for (int w = 0; w < VL; ++w)
-          q[u][w] = reinterpret_cast<const T*>(&buf[(j * NP + yy / 2) * LD + x0 + w])[yy & 1];
-        if (a.emode == E_CG) {
-          const int64_t idx = idx0 + (int64_t)j * a.N + v0 + e0;
-          vload(xv[u], a.x + idx);
-          vload(rv[u], a.r + idx);
-          vload(pv[u], a.p + idx);
-        }
-      }
+    for (int w = 0; w < VL; w += 2) {
+      C c2[2];
+      cload2<T>(c2, src + w);
+      q[0][w] = c2[0].x; q[1][w] = c2[0].y;
+      q[0][w + 1] = c2[1].x; q[1][w + 1] = c2[1].y;
     }
+    const int64_t off = (int64_t)j * a.N + v0 + (int64_t)(2 * pr) * NX + x0;
+    if (a.emode == E_CG) {
+      T xv[2][VL], rv[2][VL], pv[2][VL];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * NT + threadIdx.x;
-      if (i < ge * NV) {
-        const int j = i / NV, e0 = (i % NV) * VL;
-        const int64_t idx = idx0 + (int64_t)j * a.N + v0 + e0;
-        if (a.emode == E_CG) {
+      for (int h = 0; h < 2; ++h) {
+        vload(xv[h], a.x + idx0 + off + h * NX);
+        vload(rv[h], a.r + idx0 + off + h * NX);
+        vload(pv[h], a.p + idx0 + off + h * NX);
+      }
 #pragma unroll
-          for (int w = 0; w < VL; ++w) {
-            xv[u][w] += alpha * pv[u][w];
-            rv[u][w] -= alpha * q[u][w];
-            acc += rv[u][w] * rv[u][w];
-          }
-          vstore(a.x + idx, xv[u]);
-          vstore(a.r + idx, rv[u]);
-        } else if (a.emode == E_INIT) {
+      for (int h = 0; h < 2; ++h) {
 #pragma unroll
-          for (int w = 0; w < VL; ++w) {
-            rv[u][w] = -q[u][w];
-            xv[u][w] = 0;
-            acc += rv[u][w] * rv[u][w];
-          }
-          vstore(a.r + idx, rv[u]);
-          vstore(a.x + idx, xv[u]);
-        } else if (a.emode == E_OUT) {
-          vstore(a.out + idx, q[u]);
-        } else {  // E_NODAL: accumulate the displacement correction in FP64
-          double* u64 = a.u64 + uidx0 + (int64_t)j * a.N + v0 + e0;
-#pragma unroll
-          for (int w = 0; w < VL; ++w) u64[w] += (double)q[u][w];
+        for (int w = 0; w < VL; ++w) {
+          xv[h][w] += alpha * pv[h][w];
+          rv[h][w] -= alpha * q[h][w];
+          acc += rv[h][w] * rv[h][w];
         }
+        vstore(a.x + idx0 + off + h * NX, xv[h]);
+        vstore(a.r + idx0 + off + h * NX, rv[h]);
+      }
+    } else if (a.emode == E_INIT) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        T rv[VL], zv[VL];
+#pragma unroll
+        for (int w = 0; w < VL; ++w) {
+          rv[w] = -q[h][w];
+          zv[w] = 0;
+          acc += rv[w] * rv[w];
+        }
+        vstore(a.r + idx0 + off + h * NX, rv);
+        vstore(a.x + idx0 + off + h * NX, zv);
+      }
+    } else if (a.emode == E_OUT) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) vstore(a.out + idx0 + off + h * NX, q[h]);
+    } else {  // E_NODAL: accumulate the displacement correction in FP64
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        double* u64 = a.u64 + uidx0 + off + h * NX;
+#pragma unroll
+        for (int w = 0; w < VL; ++w) u64[w] += (double)q[h][w];
       }
     }
   }
@@ -405,7 +435,7 @@ __device__ __forceinline__ T pass_e_update(const PassArgs<T>& a, const cplx<T>* 
 // grid (n_y/TY, groups, L): groups = n_q elements (3 components each) or one
 // group of the D = 2 nodal components (E_NODAL); inverse real FFT along x.
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT) pass_e_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
@@ -456,7 +486,7 @@ cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_2d<T, NX, TY, NT>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.n[1] / TY, a.amode == A_NODAL ? 1 : 2, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -468,7 +498,7 @@ cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_2d<T, NX, TY, NT>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.n[1] / TY, a.emode == E_NODAL ? 1 : 2, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -479,7 +509,7 @@ cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 6 * FftSplit<NY>::LD;
   auto k = pass_c_2d<T, NY, NT>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.kx, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();

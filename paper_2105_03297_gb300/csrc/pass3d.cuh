@@ -28,7 +28,7 @@ __host__ __device__ constexpr int kuhn_perm(int t, int i) {
 // ---------------------------------------------------------------- pass A
 // grid (n_y/TY, n_z, L*G), G = 6 tetrahedra (6 components each) or 1 (nodal, 3).
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT) pass_a_3d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_a_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 6;
@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(NT) pass_a_3d(PassArgs<T> a) {
   T beta = 0;
   bool use_old = false;
   if (a.amode == A_CG) { beta = (T)cg->beta; use_old = cg->it > 0; }
-  const T acc = pass_a_load<T, NX, TY, GS, NT, LD>(a, buf, l, c0, ((int64_t)z * ny + y0) * NX, nodal, beta,
-                                                   use_old);
+  // two columns per unit: 6 components x 2 rows x (r, p) stay in registers
+  const T acc = pass_a_load<T, NX, TY, GS, NT, LD, 2>(a, buf, l, c0, ((int64_t)z * ny + y0) * NX, nodal, beta,
+                                                      use_old);
   __syncthreads();
   smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
   pass_a_store<T, NX, TY, NT, LD>(buf, nodal ? 3 : 6,
@@ -74,10 +75,10 @@ __global__ void __launch_bounds__(NT) pass_a_3d(PassArgs<T> a) {
 // FFT along y.  grid (n_z/TZB, n_x/2+1, L*Cc).  FWD: spec1 pencils -> spec2
 // chunks; !FWD: spec2 chunks -> spec1 pencils.
 template <typename T, int NY, int TZB, int NT, bool FWD>
-__global__ void __launch_bounds__(NT) pass_y_3d(PassArgs<T> a, int Cc) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_y_3d(PassArgs<T> a, int Cc) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LD = FftSplit<NY>::LD;
+  constexpr int LD = FftSplit<NY>::LDO;  // odd: the chunk transposes are conflict-free
   C* buf = reinterpret_cast<C*>(smem_raw);  // [TZB][LD]
   const int l = blockIdx.z / Cc, c = blockIdx.z % Cc;
   const int kx = blockIdx.y, z0 = blockIdx.x * TZB;
@@ -86,14 +87,31 @@ __global__ void __launch_bounds__(NT) pass_y_3d(PassArgs<T> a, int Cc) {
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
   const int64_t cbase = (((int64_t)l * a.m + c) * KX + kx);
+  constexpr int PER = (TZB * NY + NT - 1) / NT;
+  C v[PER];
   if (FWD) {
     const C* src = a.spec + (cbase * nz + z0) * NY;
-    for (int i = threadIdx.x; i < TZB * NY; i += NT) buf[(i / NY) * LD + (i % NY)] = src[i];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < TZB * NY) v[k] = src[i];
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < TZB * NY) buf[(i / NY) * LD + (i % NY)] = v[k];
+    }
   } else {
     const C* src = a.spec2 + cbase * NY * nz + z0;
-    for (int i = threadIdx.x; i < TZB * NY; i += NT) {
-      const int zz = i % TZB, ky = i / TZB;
-      buf[zz * LD + ky] = src[(int64_t)ky * nz + zz];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < TZB * NY) v[k] = src[(int64_t)(i / TZB) * nz + (i % TZB)];
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < TZB * NY) buf[(i % TZB) * LD + (i / TZB)] = v[k];
     }
   }
   __syncthreads();
@@ -199,7 +217,7 @@ __device__ __forceinline__ void project_3d(cplx<T>* col, const cplx<T>* e, const
 
 // grid (n_x/2+1, n_y, L): one (k_x, k_y) pencil of all components per block.
 template <typename T, int NZ, int NT>
-__global__ void __launch_bounds__(NT) pass_c_3d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 36;
   constexpr int LD = FftSplit<NZ>::LD;
@@ -214,9 +232,25 @@ __global__ void __launch_bounds__(NT) pass_c_3d(PassArgs<T> a) {
   const int cout = (a.pmode == P_NODAL_OUT) ? 3 : M;
   const int64_t stride_c = (int64_t)KX * ny * NZ;
   const C* src = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
-  for (int i = threadIdx.x; i < cin * NZ; i += NT) {
-    const int c = i / NZ, z = i % NZ;
-    buf[c * LD + z] = src[c * stride_c + z];
+  {
+    constexpr int PER = (M * NZ / 2 + NT - 1) / NT;
+    C v[PER][2];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < cin * NZ / 2) {
+        const int c = i / (NZ / 2), z = 2 * (i % (NZ / 2));
+        cload2<T>(v[k], src + c * stride_c + z);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < cin * NZ / 2) {
+        const int c = i / (NZ / 2), z = 2 * (i % (NZ / 2));
+        cstore2<T>(buf + c * LD + z, v[k][0], v[k][1]);
+      }
+    }
   }
   __syncthreads();
   if (cin == M) smem_fft<T, NZ, M, LD, NT, -1>(buf, a.tw[2]);
@@ -236,9 +270,11 @@ __global__ void __launch_bounds__(NT) pass_c_3d(PassArgs<T> a) {
   if (cout == M) smem_fft<T, NZ, M, LD, NT, +1>(buf, a.tw[2]);
   else smem_fft<T, NZ, 3, LD, NT, +1>(buf, a.tw[2]);
   C* dst = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
-  for (int i = threadIdx.x; i < cout * NZ; i += NT) {
-    const int c = i / NZ, z = i % NZ;
-    dst[c * stride_c + z] = buf[c * LD + z];
+  for (int i = threadIdx.x; i < cout * NZ / 2; i += NT) {
+    const int c = i / (NZ / 2), z = 2 * (i % (NZ / 2));
+    C v[2];
+    cload2<T>(v, buf + c * LD + z);
+    cstore2<T>(dst + c * stride_c + z, v[0], v[1]);
   }
 }
 
@@ -246,7 +282,7 @@ __global__ void __launch_bounds__(NT) pass_c_3d(PassArgs<T> a) {
 // grid (n_y/TY, n_z, L*G): G = 6 tetrahedra (6 components each) or one group
 // of the 3 nodal components (E_NODAL); inverse real FFT along x and update.
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT) pass_e_3d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
@@ -300,7 +336,7 @@ cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_3d<T, NX, TY, NT>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.amode == A_NODAL ? 1 : 6));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -312,7 +348,7 @@ cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_3d<T, NX, TY, NT>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.emode == E_NODAL ? 1 : 6));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -321,10 +357,10 @@ template <typename T, int NY, bool FWD>
 cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int TZB = Tile3D<T>::TZB;
   constexpr int NT = fft_threads<NY, TZB>();
-  const size_t sm = sizeof(cplx<T>) * TZB * FftSplit<NY>::LD;
+  const size_t sm = sizeof(cplx<T>) * TZB * FftSplit<NY>::LDO;
   auto k = pass_y_3d<T, NY, TZB, NT, FWD>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   const int Cc = FWD ? (a.pmode == P_NODAL_IN ? 3 : a.m) : (a.pmode == P_NODAL_OUT ? 3 : a.m);
   dim3 grid(a.n[2] / TZB, a.kx, a.L * Cc);
   k<<<grid, NT, sm, s>>>(a, Cc);
@@ -342,7 +378,7 @@ cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 36 * FftSplit<NZ>::LD;
   auto k = pass_c_3d<T, NZ, NT>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.kx, a.n[1], a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();

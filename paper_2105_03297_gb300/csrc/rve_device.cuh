@@ -104,6 +104,9 @@ template <int N> struct FftSplit {
   // leading dimension of one transform in shared memory (room for the padded
   // transpose of the middle step)
   static constexpr int LD = N + N2;
+  // odd leading dimension for buffers that are also read or written across
+  // transforms (transposes): consecutive transforms then fall on different banks
+  static constexpr int LDO = N + N2 + 1;
 };
 
 // Threads that give one work item per thread in both steps for NB transforms,
@@ -201,12 +204,57 @@ template <typename T> __device__ __forceinline__ void vload(T* d, const T* s) {
 #pragma unroll
   for (int i = 0; i < Vec16<T>::n; ++i) d[i] = a[i];
 }
+// Two consecutive complex values (16 bytes for float, two 16-byte halves for double)
+template <typename T> __device__ __forceinline__ void cload2(cplx<T>* d, const cplx<T>* s) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 w = *reinterpret_cast<const float4*>(s);
+    d[0] = mkc<T>(w.x, w.y); d[1] = mkc<T>(w.z, w.w);
+  } else {
+    d[0] = s[0]; d[1] = s[1];
+  }
+}
+template <typename T> __device__ __forceinline__ void cstore2(cplx<T>* d, cplx<T> a, cplx<T> b) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(d) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    d[0] = a; d[1] = b;
+  }
+}
+// VL consecutive values (VL = 2 or the 16-byte width), vectorised
+template <typename T, int VL> __device__ __forceinline__ void vloadn(T* d, const T* s) {
+  if constexpr (VL == Vec16<T>::n) {
+    vload(d, s);
+  } else if constexpr (sizeof(T) == 4 && VL == 2) {
+    const float2 w = *reinterpret_cast<const float2*>(s);
+    d[0] = w.x; d[1] = w.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < VL; ++i) d[i] = s[i];
+  }
+}
 template <typename T> __device__ __forceinline__ void vstore(T* d, const T* s) {
   typename Vec16<T>::t w;
   T* a = reinterpret_cast<T*>(&w);
 #pragma unroll
   for (int i = 0; i < Vec16<T>::n; ++i) a[i] = s[i];
   *reinterpret_cast<typename Vec16<T>::t*>(d) = w;
+}
+template <typename T, int VL> __device__ __forceinline__ void vstoren(T* d, const T* s) {
+  if constexpr (VL == Vec16<T>::n) {
+    vstore(d, s);
+  } else if constexpr (sizeof(T) == 4 && VL == 2) {
+    *reinterpret_cast<float2*>(d) = make_float2(s[0], s[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < VL; ++i) d[i] = s[i];
+  }
+}
+
+// Dynamic shared memory limit and the largest shared-memory carveout for a
+// kernel (so that as many blocks as the shared memory allows can be resident).
+template <typename K> inline void set_smem_attrs(K kernel, size_t smem) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 // ------------------------------------------------------------ reductions
