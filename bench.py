@@ -51,9 +51,10 @@ def model_bytes(dim, n, s, L_iters):
     """Algorithmic bytes of the CG-iteration passes, per load-case iteration.
 
     s: bytes per real scalar of the inner precision.  Returns dict pass -> bytes.
-    Pass A reads r, p_old and E and writes p and the x-spectrum; pass C (2D)
-    reads and writes the spectrum once; pass E reads the spectrum and x, r, p
-    and writes x and r.  In 3D passes B, C, D each read and write the spectrum.
+    Pass A reads r, p_old, x and E and writes p, x (the deferred x += alpha p)
+    and the x-spectrum; pass C (2D) reads and writes the spectrum once; pass E
+    reads the spectrum and r and writes r.  In 3D passes B, C, D each read and
+    write the spectrum.
     """
     nq, ns = (2, 3) if dim == 2 else (6, 6)
     m = nq * ns
@@ -61,9 +62,9 @@ def model_bytes(dim, n, s, L_iters):
     kx = n[0] // 2 + 1
     spec = m * kx * (N // n[0]) * 2 * s
     out = {
-        "pass_a": 3 * m * N * s + N * s + spec,
+        "pass_a": 5 * m * N * s + N * s + spec,
         "pass_c": 2 * spec,
-        "pass_e": spec + 5 * m * N * s,
+        "pass_e": spec + 2 * m * N * s,
     }
     if dim == 3:
         out["pass_b"] = 2 * spec

@@ -125,6 +125,13 @@ int rve_mean_stress(rve_t h, double* S);
  * C_eff = S^T M^-T with M[l][:] = E_macro[l]. */
 int rve_effective_tangent(rve_t h, double* C);
 
+/* Energy form of the homogenised stiffness for the solved load cases:
+ * Ce[a][b] = mean over all elements of (E_a + eps~_a) : C : (E_b + eps~_b)
+ * (host, FP64, L x L, row-major).  At the exact solution it equals
+ * E_a . C_eff E_b; its error is second order in the solve error, which makes it
+ * the quantity to difference in finite-difference checks. */
+int rve_energy_tangent(rve_t h, double* Ce);
+
 /* Adjoint gradient of J = sum_ab W[a][b] C_eff[a][b] with respect to the
  * per-voxel Young's moduli, grad_E[N] (FP64).  Needs a preceding solve with
  * L = n_s independent load cases.  For every row a of W that is not zero it

@@ -47,6 +47,7 @@ SIGNATURES = {
                             C.POINTER(rve_info)]),
     "rve_mean_stress": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "rve_effective_tangent": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "rve_energy_tangent": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "rve_adjoint": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int, C.c_void_p, C.c_int]),
     "rve_get_strain": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
@@ -175,6 +176,12 @@ class RVE:
         _check(load().rve_effective_tangent(self.h, Cm.ctypes.data_as(C.POINTER(C.c_double))),
                "rve_effective_tangent")
         return Cm
+
+    def energy_tangent(self):
+        """Energy form (E_a + eps~_a) : C : (E_b + eps~_b), averaged, for the solved load cases."""
+        Ce = np.zeros((self.L, self.L))
+        _check(load().rve_energy_tangent(self.h, Ce.ctypes.data_as(C.POINTER(C.c_double))), "rve_energy_tangent")
+        return Ce
 
     def adjoint(self, W, rel_tol=1e-10, max_iter=5000, out=None):
         W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))

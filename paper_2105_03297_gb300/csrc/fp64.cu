@@ -25,6 +25,14 @@ cudaError_t launch_homogenise(const Fp64Args& a, double* part, int* nblk_out, cu
   return cudaGetLastError();
 }
 
+cudaError_t launch_energy(const Fp64Args& a, double* part, int* nblk_out, cudaStream_t s) {
+  const int nblk = homogenise_blocks(a);
+  *nblk_out = nblk;
+  if (a.dim == 2) energy_2d<kNT><<<nblk, kNT, 0, s>>>(a, part, nblk);
+  else energy_3d<kNT><<<nblk, kNT, 0, s>>>(a, part, nblk);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_strain_field(const Fp64Args& a, int l, double* out, cudaStream_t s) {
   const unsigned nb = (unsigned)((a.N + kNT - 1) / kNT);
   if (a.dim == 2) strain_field_2d<<<nb, kNT, 0, s>>>(a, l, out);

@@ -4,4 +4,5 @@ namespace rve {
 template cudaError_t launch_pass_a_2d<double>(const PassArgs<double>&, cudaStream_t);
 template cudaError_t launch_pass_c_2d<double>(const PassArgs<double>&, cudaStream_t);
 template cudaError_t launch_pass_e_2d<double>(const PassArgs<double>&, cudaStream_t);
+template cudaError_t launch_cg_finish_x<double>(const PassArgs<double>&, cudaStream_t);
 }  // namespace rve

@@ -6,8 +6,10 @@
 //      that the next pass reads whole y-columns contiguously;
 //   C  forward FFT along y, the projection G(k) = B (B^H B)^-1 B^H per
 //      wavevector (k = 0 set to zero), inverse FFT along y, in place;
-//   E  inverse real FFT along x, then x += alpha p, r -= alpha q and <r, r>
-//      (q never touches memory).
+//   E  inverse real FFT along x, then r -= alpha q and <r, r> (q never
+//      touches memory).  x += alpha p of iteration k is deferred to pass A of
+//      iteration k+1, which reads p anyway (one vector stream less per
+//      iteration); cg_finish_x applies the last one.
 // DFT convention of Appendix A; the 1/N of the inverse is applied in pass C.
 // Two real rows (y, y+1) share one complex FFT (X_y + i X_{y+1}).
 #pragma once
@@ -52,7 +54,7 @@ __device__ __forceinline__ void finish_rr(CgState* cg, double rr, bool init) {
 // this thread's share of <p, C p>.
 template <typename T, int NX, int TY, int GS, int NT, int LD, int VL = Vec16<T>::n>
 __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int l, int c0, int64_t v0,
-                                         bool nodal, T beta, bool use_old) {
+                                         bool nodal, T beta, T alpha_prev, bool use_old) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int NU = NP * (NX / VL);
@@ -94,17 +96,28 @@ __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int
         }
       }
       if (a.amode == A_CG && use_old) {
-        T po[2][GS][VL];
+        // deferred update of the previous iteration: x += alpha_prev p_old,
+        // then the new direction p = r + beta p_old
+        T po[2][GS][VL], xo[2][GS][VL];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j) vloadn<T, VL>(po[h][j], a.p + ((int64_t)l * a.m + c0 + j) * N + va + h * NX);
+          for (int j = 0; j < GS; ++j) {
+            const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + va + h * NX;
+            vloadn<T, VL>(po[h][j], a.p + idx);
+            vloadn<T, VL>(xo[h][j], a.x + idx);
+          }
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j)
+          for (int j = 0; j < GS; ++j) {
 #pragma unroll
-            for (int q = 0; q < VL; ++q) pv[h][j][q] += beta * po[h][j][q];
+            for (int q = 0; q < VL; ++q) {
+              pv[h][j][q] += beta * po[h][j][q];
+              xo[h][j][q] += alpha_prev * po[h][j][q];
+            }
+            vstoren<T, VL>(a.x + ((int64_t)l * a.m + c0 + j) * N + va + h * NX, xo[h][j]);
+          }
       }
       if (a.amode == A_CG) {
 #pragma unroll
@@ -193,10 +206,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_a_2d(PassArgs
   if (a.cgphase && cg->status != ST_RUN) return;
   const bool nodal = (a.amode == A_NODAL);
   const int c0 = nodal ? 0 : grp * 3;
-  T beta = 0;
+  T beta = 0, alpha_prev = 0;
   bool use_old = false;
-  if (a.amode == A_CG) { beta = (T)cg->beta; use_old = cg->it > 0; }
-  const T acc = pass_a_load<T, NX, TY, GS, NT, LD>(a, buf, l, c0, (int64_t)y0 * NX, nodal, beta, use_old);
+  if (a.amode == A_CG) { beta = (T)cg->beta; alpha_prev = (T)cg->alpha; use_old = cg->it > 0; }
+  const T acc = pass_a_load<T, NX, TY, GS, NT, LD>(a, buf, l, c0, (int64_t)y0 * NX, nodal, beta, alpha_prev,
+                                                   use_old);
   __syncthreads();
   smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
   pass_a_store<T, NX, TY, NT, LD>(buf, nodal ? 2 : 3, a.spec + (((int64_t)l * a.m + c0) * KX) * ny + y0,
@@ -266,7 +280,10 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
   }
 }
 
-// grid (n_x/2+1, L); one k_x column of all six spectra per block.
+// grid (n_x/2+1, L); one k_x column of all six spectra per block.  The forward
+// FFT reads the column straight from the spectrum, the inverse FFT writes it
+// straight back; only the middle transposes and the projection use shared
+// memory.
 template <typename T, int NY, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
@@ -281,31 +298,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs
   if (a.cgphase && cg->status != ST_RUN) return;
   const int cin = (a.pmode == P_NODAL_IN) ? 2 : M;
   const int cout = (a.pmode == P_NODAL_OUT) ? 2 : M;
-  const C* src = a.spec + (((int64_t)l * M) * KX + kx) * NY;
-  {
-    // batched 2-complex loads: all of a thread's loads are in flight together
-    constexpr int PER = (M * NY / 2 + NT - 1) / NT;
-    C v[PER][2];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < cin * NY / 2) {
-        const int c = i / (NY / 2), y = 2 * (i % (NY / 2));
-        cload2<T>(v[k], src + (int64_t)c * KX * NY + y);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < cin * NY / 2) {
-        const int c = i / (NY / 2), y = 2 * (i % (NY / 2));
-        cstore2<T>(buf + c * LD + y, v[k][0], v[k][1]);
-      }
-    }
-  }
-  __syncthreads();
-  if (cin == M) smem_fft<T, NY, M, LD, NT, -1>(buf, a.tw[1]);
-  else smem_fft<T, NY, 2, LD, NT, -1>(buf, a.tw[1]);
+  C* col = a.spec + (((int64_t)l * M) * KX + kx) * NY;
+  const int64_t cstride = (int64_t)KX * NY;
+  auto ld_g = [&](int c, int y) -> C { return col[c * cstride + y]; };
+  auto st_s = [&](int c, int k, C v) { buf[c * LD + k] = v; };
+  if (cin == M) fft4<T, NY, M, LD, NT, -1, false, true, false, false>(buf, a.tw[1], ld_g, st_s);
+  else fft4<T, NY, 2, LD, NT, -1, false, true, false, false>(buf, a.tw[1], ld_g, st_s);
 
   const C ex = a.ph[0][kx];
   for (int ky = threadIdx.x; ky < NY; ky += NT) {
@@ -323,15 +321,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs
       if (c < cout) buf[c * LD + ky] = s[c];
   }
   __syncthreads();
-  if (cout == M) smem_fft<T, NY, M, LD, NT, +1>(buf, a.tw[1]);
-  else smem_fft<T, NY, 2, LD, NT, +1>(buf, a.tw[1]);
-  C* dst = a.spec + (((int64_t)l * M) * KX + kx) * NY;
-  for (int i = threadIdx.x; i < cout * NY / 2; i += NT) {
-    const int c = i / (NY / 2), y = 2 * (i % (NY / 2));
-    C v[2];
-    cload2<T>(v, buf + c * LD + y);
-    cstore2<T>(dst + (int64_t)c * KX * NY + y, v[0], v[1]);
-  }
+  auto ld_s = [&](int c, int y) -> C { return buf[c * LD + y]; };
+  auto st_g = [&](int c, int k, C v) { col[c * cstride + k] = v; };
+  if (cout == M) fft4<T, NY, M, LD, NT, +1, true, false, false, false>(buf, a.tw[1], ld_s, st_g);
+  else fft4<T, NY, 2, LD, NT, +1, true, false, false, false>(buf, a.tw[1], ld_s, st_g);
 }
 
 // ------------------------------------------------------------------------
@@ -356,80 +349,78 @@ __device__ __forceinline__ void pass_e_unpack(cplx<T>* buf, const cplx<T>* src, 
   }
 }
 
-// Per-voxel update of ge components over the tile of TY rows starting at
-// voxel v0; q of component j, rows (2 pr, 2 pr + 1), is the real / imaginary
-// part of the packed row j*NP + pr.  A thread handles two rows x VL columns of
-// one component.  idx0 / uidx0: offsets of the first component's [N] slab in
-// the CG vectors / the FP64 nodal field (components follow at stride N).
-// Returns the thread's share of <r, r>.
-template <typename T, int NX, int TY, int NT, int LD>
-__device__ __forceinline__ T pass_e_update(const PassArgs<T>& a, const cplx<T>* buf, int ge, int64_t v0,
-                                           int64_t idx0, int64_t uidx0, T alpha) {
-  using C = cplx<T>;
-  constexpr int VL = Vec16<T>::n;
-  constexpr int NP = TY / 2;
-  constexpr int NU = NP * (NX / VL);
-  static_assert(LD % 2 == 0, "row starts must stay 16-byte aligned");
-  T acc = 0;
-  for (int i = threadIdx.x; i < ge * NU; i += NT) {
-    const int j = i / NU, iu = i % NU;
-    const int pr = iu / (NX / VL), x0 = (iu % (NX / VL)) * VL;
-    T q[2][VL];
-    const C* src = buf + (j * NP + pr) * LD + x0;
+// The inverse FFT of pass E hands each output q(b, x) (b = j*NP + pr: rows
+// 2 pr and 2 pr + 1 of component j, real and imaginary part) to this update:
+// CG: r -= alpha q and <r, r>; INIT: r = -q, x = 0; OUT: out = q; NODAL: u += q
+// in FP64.  Consecutive threads handle consecutive x, so every access is
+// coalesced.  idx0 / uidx0: offsets of the first component's [N] slab in the
+// CG vectors / the FP64 nodal field; v0: first voxel of the tile.
+template <typename T, int NX, int NP>
+struct PassEStore {
+  const PassArgs<T>* a;
+  int ge;
+  int64_t v0, idx0, uidx0;
+  T alpha;
+  T* acc;
+  // outputs x = k2 + N2 k1 (k1 < N1) of rows (2 pr, 2 pr + 1) of component j:
+  // all loads of r (or u) are issued before any store
+  __device__ __forceinline__ void batch(int b, int k2, const cplx<T>* q) const {
+    constexpr int N1 = FftSplit<NX>::N1, N2 = FftSplit<NX>::N2;
+    const int j = b / NP, pr = b % NP;
+    if (j >= ge) return;
+    const int64_t off = (int64_t)j * a->N + v0 + (int64_t)(2 * pr) * NX + k2;
+    const int em = a->emode;
+    if (em == E_CG) {
+      // chunks of up to 16 outputs: 32 loads in flight, bounded registers
+      constexpr int CH = N1 < 16 ? N1 : 16;
+      T* r = a->r + idx0 + off;
+      T s = 0;
 #pragma unroll
-    for (int w = 0; w < VL; w += 2) {
-      C c2[2];
-      cload2<T>(c2, src + w);
-      q[0][w] = c2[0].x; q[1][w] = c2[0].y;
-      q[0][w + 1] = c2[1].x; q[1][w + 1] = c2[1].y;
-    }
-    const int64_t off = (int64_t)j * a.N + v0 + (int64_t)(2 * pr) * NX + x0;
-    if (a.emode == E_CG) {
-      T xv[2][VL], rv[2][VL], pv[2][VL];
+      for (int c0 = 0; c0 < N1; c0 += CH) {
+        T rv[2][CH];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        vload(xv[h], a.x + idx0 + off + h * NX);
-        vload(rv[h], a.r + idx0 + off + h * NX);
-        vload(pv[h], a.p + idx0 + off + h * NX);
-      }
+        for (int k = 0; k < CH; ++k) { rv[0][k] = r[N2 * (c0 + k)]; rv[1][k] = r[NX + N2 * (c0 + k)]; }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int w = 0; w < VL; ++w) {
-          xv[h][w] += alpha * pv[h][w];
-          rv[h][w] -= alpha * q[h][w];
-          acc += rv[h][w] * rv[h][w];
+        for (int k = 0; k < CH; ++k) {
+          rv[0][k] -= alpha * q[c0 + k].x;
+          rv[1][k] -= alpha * q[c0 + k].y;
+          s += rv[0][k] * rv[0][k] + rv[1][k] * rv[1][k];
+          r[N2 * (c0 + k)] = rv[0][k];
+          r[NX + N2 * (c0 + k)] = rv[1][k];
         }
-        vstore(a.x + idx0 + off + h * NX, xv[h]);
-        vstore(a.r + idx0 + off + h * NX, rv[h]);
       }
-    } else if (a.emode == E_INIT) {
+      *acc += s;
+    } else if (em == E_INIT) {
+      T* r = a->r + idx0 + off;
+      T* x = a->x + idx0 + off;
+      T s = 0;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        T rv[VL], zv[VL];
-#pragma unroll
-        for (int w = 0; w < VL; ++w) {
-          rv[w] = -q[h][w];
-          zv[w] = 0;
-          acc += rv[w] * rv[w];
-        }
-        vstore(a.r + idx0 + off + h * NX, rv);
-        vstore(a.x + idx0 + off + h * NX, zv);
+      for (int k1 = 0; k1 < N1; ++k1) {
+        r[N2 * k1] = -q[k1].x;
+        r[NX + N2 * k1] = -q[k1].y;
+        x[N2 * k1] = 0;
+        x[NX + N2 * k1] = 0;
+        s += q[k1].x * q[k1].x + q[k1].y * q[k1].y;
       }
-    } else if (a.emode == E_OUT) {
+      *acc += s;
+    } else if (em == E_OUT) {
+      T* o = a->out + idx0 + off;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) vstore(a.out + idx0 + off + h * NX, q[h]);
-    } else {  // E_NODAL: accumulate the displacement correction in FP64
+      for (int k1 = 0; k1 < N1; ++k1) { o[N2 * k1] = q[k1].x; o[NX + N2 * k1] = q[k1].y; }
+    } else {
+      double* u = a->u64 + uidx0 + off;
+      double uv[2][N1];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        double* u64 = a.u64 + uidx0 + off + h * NX;
+      for (int k1 = 0; k1 < N1; ++k1) { uv[0][k1] = u[N2 * k1]; uv[1][k1] = u[NX + N2 * k1]; }
 #pragma unroll
-        for (int w = 0; w < VL; ++w) u64[w] += (double)q[h][w];
+      for (int k1 = 0; k1 < N1; ++k1) {
+        u[N2 * k1] = uv[0][k1] + (double)q[k1].x;
+        u[NX + N2 * k1] = uv[1][k1] + (double)q[k1].y;
       }
     }
   }
-  return acc;
-}
+  __device__ __forceinline__ void operator()(int, int, cplx<T>) const {}
+};
 
 // ---------------------------------------------------------------- pass E
 // grid (n_y/TY, groups, L): groups = n_q elements (3 components each) or one
@@ -457,10 +448,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_2d(PassArgs
 
   pass_e_unpack<T, NX, TY, NT, LD>(buf, a.spec + (((int64_t)l * a.m + c0) * KX) * ny + y0, ge, (int64_t)KX * ny, ny);
   __syncthreads();
-  smem_fft<T, NX, GE * NP, LD, NT, +1>(buf, a.tw[0]);
+  T acc = 0;
   const T alpha = (a.emode == E_CG) ? (T)cg->alpha : (T)0;
-  const T acc = pass_e_update<T, NX, TY, NT, LD>(a, buf, ge, (int64_t)y0 * NX, ((int64_t)l * a.m + c0) * N,
-                                                 (int64_t)l * 2 * N, alpha);
+  auto ld_s = [&](int b, int x) -> C { return buf[b * LD + x]; };
+  PassEStore<T, NX, NP> st{&a, ge, (int64_t)y0 * NX, ((int64_t)l * a.m + c0) * N, (int64_t)l * 2 * N, alpha, &acc};
+  fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
+                                                                                                  ld_s, st);
 
   if (a.emode == E_CG || a.emode == E_INIT) {
     const double s = block_sum<NT>((double)acc, red);
@@ -472,6 +465,35 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_2d(PassArgs
       if (threadIdx.x == 0) finish_rr(cg, rr, a.emode == E_INIT);
     }
   }
+}
+
+// x += alpha p for every load case that ran at least one iteration: the
+// update the last CG iteration deferred.  grid (ceil(m N / (VL*NT)), L).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) cg_finish_x(PassArgs<T> a) {
+  constexpr int VL = Vec16<T>::n;
+  const int l = blockIdx.y;
+  const CgState* cg = a.cg + l;
+  if (!cg->active || cg->it == 0 || cg->status == ST_BAD) return;
+  const T alpha = (T)cg->alpha;
+  const int64_t nv = (int64_t)a.m * a.N / VL;
+  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (i >= nv) return;
+  const int64_t idx = (int64_t)l * a.m * a.N + i * VL;
+  T xv[VL], pv[VL];
+  vload(xv, a.x + idx);
+  vload(pv, a.p + idx);
+#pragma unroll
+  for (int w = 0; w < VL; ++w) xv[w] += alpha * pv[w];
+  vstore(a.x + idx, xv);
+}
+
+template <typename T> cudaError_t launch_cg_finish_x(const PassArgs<T>& a, cudaStream_t s) {
+  constexpr int NT = 256;
+  const int64_t nv = (int64_t)a.m * a.N / Vec16<T>::n;
+  dim3 grid((unsigned)((nv + NT - 1) / NT), a.L);
+  cg_finish_x<T, NT><<<grid, NT, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ launchers

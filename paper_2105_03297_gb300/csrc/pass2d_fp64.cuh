@@ -141,6 +141,37 @@ __global__ void __launch_bounds__(NT) homogenise_2d(Fp64Args a, double* part, in
   }
 }
 
+// Block partial sums of eps_a : C : eps_b over the elements, for the pairs
+// a <= b of the L solved load cases: part[p * nblk + blk].
+template <int NT>
+__global__ void __launch_bounds__(NT) energy_2d(Fp64Args a, double* part, int nblk) {
+  __shared__ double red[NT / 32];
+  const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const bool ok = v < a.N;
+  const int x = ok ? (int)(v % a.n[0]) : 0, y = ok ? (int)(v / a.n[0]) : 0;
+  const double e = ok ? a.E[v] : 0.0;
+  int p = 0;
+  for (int lb = 0; lb < a.L; ++lb) {
+    double sb[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    if (ok) {
+      double eb[2][3];
+      strain_2d(a.u + (int64_t)lb * 2 * a.N, a.N, a.n[0], a.n[1], x, y, a.emac + lb * 3, a.ih[0], a.ih[1], eb);
+      for (int q = 0; q < 2; ++q) stress_2d(eb[q], e, a.lam, a.mu2, sb[q]);
+    }
+    for (int la = 0; la <= lb; ++la, ++p) {
+      double t = 0.0;
+      if (ok) {
+        double ea[2][3];
+        strain_2d(a.u + (int64_t)la * 2 * a.N, a.N, a.n[0], a.n[1], x, y, a.emac + la * 3, a.ih[0], a.ih[1], ea);
+        for (int q = 0; q < 2; ++q)
+          for (int s = 0; s < 3; ++s) t += ea[q][s] * sb[q][s];
+      }
+      const double bs = block_sum<NT>(t, red);
+      if (threadIdx.x == 0) part[(int64_t)p * nblk + blockIdx.x] = bs;
+    }
+  }
+}
+
 // Total strain field eps[m][N] (FP64) of load case l.
 __global__ void strain_field_2d(Fp64Args a, int l, double* out) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

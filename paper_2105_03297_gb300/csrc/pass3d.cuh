@@ -8,7 +8,8 @@
 //   C  forward FFT along z, projection G(k) per wavevector, inverse FFT along
 //      z, in place on spec2 (all m = 36 components of one (k_x, k_y) pencil);
 //   D  inverse FFT along y, spec2 -> spec1;
-//   E  inverse real FFT along x, x += alpha p, r -= alpha q, <r, r>.
+//   E  inverse real FFT along x, r -= alpha q, <r, r> (x += alpha p is
+//      deferred to the next pass A, as in 2D).
 #pragma once
 #include "pass2d.cuh"
 
@@ -47,12 +48,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_a_3d(PassArgs
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
   const int c0 = nodal ? 0 : grp * 6;
-  T beta = 0;
+  T beta = 0, alpha_prev = 0;
   bool use_old = false;
-  if (a.amode == A_CG) { beta = (T)cg->beta; use_old = cg->it > 0; }
-  // two columns per unit: 6 components x 2 rows x (r, p) stay in registers
+  if (a.amode == A_CG) { beta = (T)cg->beta; alpha_prev = (T)cg->alpha; use_old = cg->it > 0; }
+  // two columns per unit: 6 components x 2 rows x (r, p, x) stay in registers
   const T acc = pass_a_load<T, NX, TY, GS, NT, LD, 2>(a, buf, l, c0, ((int64_t)z * ny + y0) * NX, nodal, beta,
-                                                      use_old);
+                                                      alpha_prev, use_old);
   __syncthreads();
   smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
   pass_a_store<T, NX, TY, NT, LD>(buf, nodal ? 3 : 6,
@@ -87,44 +88,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_y_3d(PassArgs
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
   const int64_t cbase = (((int64_t)l * a.m + c) * KX + kx);
-  constexpr int PER = (TZB * NY + NT - 1) / NT;
-  C v[PER];
+  C* pencils = a.spec + (cbase * nz + z0) * NY;  // [zz][y], y contiguous
+  C* chunks = a.spec2 + cbase * NY * nz + z0;     // [k_y][zz], zz contiguous
   if (FWD) {
-    const C* src = a.spec + (cbase * nz + z0) * NY;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < TZB * NY) v[k] = src[i];
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < TZB * NY) buf[(i / NY) * LD + (i % NY)] = v[k];
-    }
+    // step 1 reads whole y-pencils, step 2 writes z-chunks (zz fastest)
+    auto ld = [&](int zz, int y) -> C { return pencils[(int64_t)zz * NY + y]; };
+    auto st = [&](int zz, int k, C v) { chunks[(int64_t)k * nz + zz] = v; };
+    fft4<T, NY, TZB, LD, NT, -1, false, false, false, true>(buf, a.tw[1], ld, st);
   } else {
-    const C* src = a.spec2 + cbase * NY * nz + z0;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < TZB * NY) v[k] = src[(int64_t)(i / TZB) * nz + (i % TZB)];
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < TZB * NY) buf[(i % TZB) * LD + (i / TZB)] = v[k];
-    }
-  }
-  __syncthreads();
-  smem_fft<T, NY, TZB, LD, NT, FWD ? -1 : +1>(buf, a.tw[1]);
-  if (FWD) {
-    C* dst = a.spec2 + cbase * NY * nz + z0;
-    for (int i = threadIdx.x; i < TZB * NY; i += NT) {
-      const int zz = i % TZB, ky = i / TZB;
-      dst[(int64_t)ky * nz + zz] = buf[zz * LD + ky];
-    }
-  } else {
-    C* dst = a.spec + (cbase * nz + z0) * NY;
-    for (int i = threadIdx.x; i < TZB * NY; i += NT) dst[i] = buf[(i / NY) * LD + (i % NY)];
+    auto ld = [&](int zz, int k) -> C { return chunks[(int64_t)k * nz + zz]; };
+    auto st = [&](int zz, int y, C v) { pencils[(int64_t)zz * NY + y] = v; };
+    fft4<T, NY, TZB, LD, NT, +1, false, false, true, false>(buf, a.tw[1], ld, st);
   }
 }
 
@@ -231,30 +205,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
   const int cin = (a.pmode == P_NODAL_IN) ? 3 : M;
   const int cout = (a.pmode == P_NODAL_OUT) ? 3 : M;
   const int64_t stride_c = (int64_t)KX * ny * NZ;
-  const C* src = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
-  {
-    constexpr int PER = (M * NZ / 2 + NT - 1) / NT;
-    C v[PER][2];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < cin * NZ / 2) {
-        const int c = i / (NZ / 2), z = 2 * (i % (NZ / 2));
-        cload2<T>(v[k], src + c * stride_c + z);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < cin * NZ / 2) {
-        const int c = i / (NZ / 2), z = 2 * (i % (NZ / 2));
-        cstore2<T>(buf + c * LD + z, v[k][0], v[k][1]);
-      }
-    }
-  }
-  __syncthreads();
-  if (cin == M) smem_fft<T, NZ, M, LD, NT, -1>(buf, a.tw[2]);
-  else smem_fft<T, NZ, 3, LD, NT, -1>(buf, a.tw[2]);
+  C* pen = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
+  auto ld_g = [&](int c, int z) -> C { return pen[c * stride_c + z]; };
+  auto st_s = [&](int c, int k, C v) { buf[c * LD + k] = v; };
+  if (cin == M) fft4<T, NZ, M, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
+  else fft4<T, NZ, 3, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
   C e[3];
   e[0] = a.ph[0][kx];
   e[1] = a.ph[1][ky];
@@ -267,15 +222,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
     }
   }
   __syncthreads();
-  if (cout == M) smem_fft<T, NZ, M, LD, NT, +1>(buf, a.tw[2]);
-  else smem_fft<T, NZ, 3, LD, NT, +1>(buf, a.tw[2]);
-  C* dst = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
-  for (int i = threadIdx.x; i < cout * NZ / 2; i += NT) {
-    const int c = i / (NZ / 2), z = 2 * (i % (NZ / 2));
-    C v[2];
-    cload2<T>(v, buf + c * LD + z);
-    cstore2<T>(dst + c * stride_c + z, v[0], v[1]);
-  }
+  auto ld_s = [&](int c, int z) -> C { return buf[c * LD + z]; };
+  auto st_g = [&](int c, int k, C v) { pen[c * stride_c + k] = v; };
+  if (cout == M) fft4<T, NZ, M, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
+  else fft4<T, NZ, 3, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
 }
 
 // ---------------------------------------------------------------- pass E
@@ -307,10 +257,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_3d(PassArgs
   pass_e_unpack<T, NX, TY, NT, LD>(buf, a.spec + ((((int64_t)l * a.m + c0) * KX) * nz + z) * ny + y0, ge,
                                    (int64_t)KX * nz * ny, (int64_t)nz * ny);
   __syncthreads();
-  smem_fft<T, NX, GE * NP, LD, NT, +1>(buf, a.tw[0]);
+  T acc = 0;
   const T alpha = (a.emode == E_CG) ? (T)cg->alpha : (T)0;
-  const T acc = pass_e_update<T, NX, TY, NT, LD>(a, buf, ge, ((int64_t)z * ny + y0) * NX,
-                                                 ((int64_t)l * a.m + c0) * N, (int64_t)l * 3 * N, alpha);
+  auto ld_s = [&](int b, int x) -> C { return buf[b * LD + x]; };
+  PassEStore<T, NX, NP> st{&a, ge, ((int64_t)z * ny + y0) * NX, ((int64_t)l * a.m + c0) * N, (int64_t)l * 3 * N,
+                           alpha, &acc};
+  fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
+                                                                                                  ld_s, st);
 
   if (a.emode == E_CG || a.emode == E_INIT) {
     const double s = block_sum<NT>((double)acc, red);

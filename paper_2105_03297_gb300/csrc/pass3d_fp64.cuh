@@ -185,6 +185,37 @@ __global__ void __launch_bounds__(NT) homogenise_3d(Fp64Args a, double* part, in
   }
 }
 
+// Block partial sums of eps_a : C : eps_b (pairs a <= b): part[p * nblk + blk].
+template <int NT>
+__global__ void __launch_bounds__(NT) energy_3d(Fp64Args a, double* part, int nblk) {
+  __shared__ double red[NT / 32];
+  const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const bool ok = v < a.N;
+  const int x = ok ? (int)(v % a.n[0]) : 0, y = ok ? (int)((v / a.n[0]) % a.n[1]) : 0;
+  const int z = ok ? (int)(v / ((int64_t)a.n[0] * a.n[1])) : 0;
+  const double e = ok ? a.E[v] : 0.0;
+  int p = 0;
+  for (int lb = 0; lb < a.L; ++lb) {
+    double sb[6][6];
+    if (ok) {
+      double eb[6][6];
+      strain_3d(a.u + (int64_t)lb * 3 * a.N, a.N, a.n, x, y, z, a.emac + lb * 6, a.ih, eb);
+      for (int t = 0; t < 6; ++t) stress_3d(eb[t], e, a.lam, a.mu2, sb[t]);
+    }
+    for (int la = 0; la <= lb; ++la, ++p) {
+      double acc = 0.0;
+      if (ok) {
+        double ea[6][6];
+        strain_3d(a.u + (int64_t)la * 3 * a.N, a.N, a.n, x, y, z, a.emac + la * 6, a.ih, ea);
+        for (int t = 0; t < 6; ++t)
+          for (int s = 0; s < 6; ++s) acc += ea[t][s] * sb[t][s];
+      }
+      const double bs = block_sum<NT>(acc, red);
+      if (threadIdx.x == 0) part[(int64_t)p * nblk + blockIdx.x] = bs;
+    }
+  }
+}
+
 __global__ void strain_field_3d(Fp64Args a, int l, double* out) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.N) return;

@@ -356,6 +356,8 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
         if (active[l] && h->cg_h[l].status == ST_RUN) running = true;
       if (!running) break;
     }
+    // apply the x update the last iteration deferred
+    CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<T>(a, h->stream); }));
     if ((rc = read_state(h, L))) return rc;
     for (int l = 0; l < L; ++l) {
       if (!active[l]) continue;
@@ -593,6 +595,36 @@ int rve_effective_tangent(rve_t h, double* C) {
       double v = 0.0;
       for (int l = 0; l < ns; ++l) v += h->S_h[(size_t)l * ns + s] * Minv[(size_t)t * ns + l];
       C[s * ns + t] = v;
+    }
+  return RVE_OK;
+}
+
+int rve_energy_tangent(rve_t h, double* Ce) {
+  if (!h || !Ce || !h->solved) return RVE_ERR_ARG;
+  const int L = h->L_solved;
+  const int npair = L * (L + 1) / 2;
+  Fp64Args fa = fp64_args(h, L, h->u, h->emac_d, h->cg);
+  const int nblk = homogenise_blocks(fa);
+  const size_t need = (size_t)npair * nblk;
+  if ((int64_t)need > h->hpart_cap) {
+    free_devp(h->hpart);
+    int rc = dev_alloc((void**)&h->hpart, need * sizeof(double));
+    if (rc) return rc;
+    h->hpart_cap = (int)need;
+  }
+  int nb = 0;
+  CK(timed(h, K_OTHER, [&] { return launch_energy(fa, h->hpart, &nb, h->stream); }));
+  std::vector<double> hp(need);
+  CK(cudaMemcpyAsync(hp.data(), h->hpart, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) flush_timing(h);
+  const double scale = 1.0 / ((double)h->N * h->nq);
+  int p = 0;
+  for (int b = 0; b < L; ++b)
+    for (int a = 0; a <= b; ++a, ++p) {
+      double t = 0.0;
+      for (int k = 0; k < nb; ++k) t += hp[(size_t)p * nb + k];
+      Ce[a * L + b] = Ce[b * L + a] = t * scale;
     }
   return RVE_OK;
 }

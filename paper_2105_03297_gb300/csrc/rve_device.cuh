@@ -194,6 +194,89 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
   __syncthreads();
 }
 
+// Four-step FFT with caller-supplied input and output (same algorithm as
+// smem_fft): step 1 reads its inputs through load(b, n) (n = n1 + N1 n2), step 2
+// hands every output to store(b, k, value) (k = k2 + N2 k1).  The middle
+// transpose lives in buf (leading dimension LD >= N + N2 per transform).
+//   LOAD_SMEM:  load() reads buf, so the middle transpose waits for all loads;
+//   STORE_SMEM: store() writes buf, so the stores wait for all step-2 reads;
+//   B1_FAST / B2_FAST: work items of step 1 / step 2 are ordered with the
+//   transform index b fastest (else n1 / k2 fastest), to match the global
+//   layout the load / store touches;
+//   BATCH_STORE: store.batch(b, k2, v) receives the N1 outputs of an item at
+//   once (k = k2 + N2 k1), so that it can issue all of its global loads first.
+template <typename T, int N, int NB, int LD, int NT, int S, bool LOAD_SMEM, bool STORE_SMEM, bool B1_FAST,
+          bool B2_FAST, class Load, class Store, bool BATCH_STORE = false>
+__device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ tw, Load load, Store store) {
+  using C = cplx<T>;
+  constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
+  static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
+  constexpr int W1 = NB * N1, W2 = NB * N2;
+  constexpr int I1 = (W1 + NT - 1) / NT, I2 = (W2 + NT - 1) / NT;
+  {
+    C v[I1][N2];
+#pragma unroll
+    for (int i = 0; i < I1; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W1 % NT) == 0 || it < W1) {
+        const int b = B1_FAST ? it % NB : it / N1, n1 = B1_FAST ? it / NB : it % N1;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v[i][n2] = load(b, n1 + N1 * n2);
+      }
+    }
+    if (LOAD_SMEM) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < I1; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W1 % NT) == 0 || it < W1) {
+        const int b = B1_FAST ? it % NB : it / N1, n1 = B1_FAST ? it / NB : it % N1;
+        fft_reg<N2, S>(v[i]);
+        C* dst = buf + b * LD + n1;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          C t = v[i][k2];
+          if (k2 > 0 && n1 > 0) {
+            C w = __ldg(tw + n1 * k2);
+            if (S > 0) w.y = -w.y;
+            t = cmul(t, w);
+          }
+          dst[k2 * (N1 + 1)] = t;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    C v[I2][N1];
+#pragma unroll
+    for (int i = 0; i < I2; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W2 % NT) == 0 || it < W2) {
+        const int b = B2_FAST ? it % NB : it / N2, k2 = B2_FAST ? it / NB : it % N2;
+        const C* src = buf + b * LD + k2 * (N1 + 1);
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[i][n1] = src[n1];
+      }
+    }
+    if (STORE_SMEM) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < I2; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if ((W2 % NT) == 0 || it < W2) {
+        const int b = B2_FAST ? it % NB : it / N2, k2 = B2_FAST ? it / NB : it % N2;
+        fft_reg<N1, S>(v[i]);
+        if constexpr (BATCH_STORE) {
+          store.batch(b, k2, v[i]);  // outputs k = k2 + N2 k1, k1 < N1, in one call
+        } else {
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) store(b, k2 + N2 * k1, v[i][k1]);
+        }
+      }
+    }
+  }
+  if (STORE_SMEM) __syncthreads();
+}
+
 // 16-byte vector of T (4 floats or 2 doubles) for the streaming loops.
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using t = float4; static constexpr int n = 4; };

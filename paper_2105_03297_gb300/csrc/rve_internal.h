@@ -18,7 +18,7 @@ enum PassAMode {
 };
 // Modes of the last pass (inverse x-FFT + update)
 enum PassEMode {
-  E_CG = 0,      // x += alpha p ; r -= alpha q ; <r, r> -> beta, convergence
+  E_CG = 0,      // r -= alpha q ; <r, r> -> beta, convergence
   E_INIT = 1,    // r = -q ; x = 0 ; <r, r> -> rr0
   E_OUT = 2,     // out = q (m components)
   E_NODAL = 3    // u64 += q (D nodal components, accumulated in FP64)
@@ -80,6 +80,8 @@ template <typename T> cudaError_t launch_pass_a_2d(const PassArgs<T>& a, cudaStr
 template <typename T> cudaError_t launch_pass_c_2d(const PassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_pass_e_2d(const PassArgs<T>& a, cudaStream_t s);
 
+template <typename T> cudaError_t launch_cg_finish_x(const PassArgs<T>& a, cudaStream_t s);
+
 template <typename T> cudaError_t launch_pass_a_3d(const PassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_pass_b_3d(const PassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_pass_c_3d(const PassArgs<T>& a, cudaStream_t s);
@@ -90,6 +92,8 @@ cudaError_t launch_residual(const Fp64Args& a, cudaStream_t s);
 // part[(l*ns + s)*nblk + blk]; returns nblk through *nblk_out
 cudaError_t launch_homogenise(const Fp64Args& a, double* part, int* nblk_out, cudaStream_t s);
 int homogenise_blocks(const Fp64Args& a);
+// part[p * nblk + blk] for the pairs p of (a <= b), a, b < L; returns nblk
+cudaError_t launch_energy(const Fp64Args& a, double* part, int* nblk_out, cudaStream_t s);
 cudaError_t launch_strain_field(const Fp64Args& a, int l, double* out, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const Fp64Args& a, const double* uadj, const double* W, const int* has_adj,
                                 double scale, double* grad, cudaStream_t s);
