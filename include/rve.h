@@ -164,6 +164,28 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
 int rve_timing_enable(rve_t h, int enable);
 int rve_timing_read(rve_t h, double* ms /*[RVE_NKINDS]*/, int64_t* launches /*[RVE_NKINDS]*/);
 
+/* ---- Batches of RVEs of uneven grid size -------------------------------
+ * A batch holds `count` RVEs of one dimension and precision, each with its own
+ * grid (same size rules as rve_create) and per-voxel moduli, and one Poisson
+ * ratio.  RVEs of equal grid size form a group whose RVEs x load cases are
+ * solved together as batch slots of one set of launches (every slot has its own
+ * CG scalars and stops on its own); the groups run concurrently on streams of
+ * their own.  The batch owns all device memory; calls return after the work is
+ * done. */
+typedef struct rve_batch_s* rve_batch_t;
+
+/* n[count * dim] grid sizes (x first per RVE). */
+int rve_batch_create(rve_batch_t* out, int dim, int count, const int64_t* n, int precision, double nu);
+int rve_batch_destroy(rve_batch_t b);
+/* Moduli of RVE `index` (same rules as rve_set_material). */
+int rve_batch_set_material(rve_batch_t b, int index, const void* E, int E_dtype, int ptr_flags);
+/* Solve the L load cases E_macro[L][n_s] for every RVE; info[count][L] (may be
+ * NULL).  Returns the worst status over all slots. */
+int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info);
+/* Mean stresses S[L][n_s] / effective tangent C[n_s][n_s] (L = n_s) of RVE `index`. */
+int rve_batch_mean_stress(rve_batch_t b, int index, double* S);
+int rve_batch_effective_tangent(rve_batch_t b, int index, double* C);
+
 /* Allocation-free operator application (the paper has no counterpart; this is
  * a service for callers that cannot allocate device memory, e.g. code inside
  * an application that owns the whole device memory pool through its own

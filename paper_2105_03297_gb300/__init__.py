@@ -7,8 +7,8 @@ behind the C ABI of ``include/rve.h``.  This package is the thin Python
 binding (``RVE``) and the ``torch.autograd.Function`` of the effective
 stiffness.
 """
-from ._rve import (RVE, RVE_ERR_ARG, RVE_ERR_NONFINITE, RVE_ERR_NOT_CONVERGED, RVE_ERR_UNSUPPORTED_SIZE,
+from ._rve import (RVE, RVEBatch, RVE_ERR_ARG, RVE_ERR_NONFINITE, RVE_ERR_NOT_CONVERGED, RVE_ERR_UNSUPPORTED_SIZE,
                    RVE_OK, RveError, load)
 
-__all__ = ["RVE", "RveError", "load", "RVE_OK", "RVE_ERR_ARG", "RVE_ERR_NONFINITE",
+__all__ = ["RVE", "RVEBatch", "RveError", "load", "RVE_OK", "RVE_ERR_ARG", "RVE_ERR_NONFINITE",
            "RVE_ERR_NOT_CONVERGED", "RVE_ERR_UNSUPPORTED_SIZE"]

@@ -55,6 +55,14 @@ SIGNATURES = {
     "rve_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "rve_apply_operator_2d_static": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_void_p,
                                                C.c_double, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "rve_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_int,
+                                   C.c_double]),
+    "rve_batch_destroy": (C.c_int, [C.c_void_p]),
+    "rve_batch_set_material": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "rve_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int,
+                                  C.POINTER(rve_info)]),
+    "rve_batch_mean_stress": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "rve_batch_effective_tangent": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "rve_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                             C.POINTER(C.c_int)]),
 }
@@ -221,3 +229,65 @@ class RVE:
         assert flag == flag2
         _check(load().rve_apply_operator(self.h, pp, qp, 1 if material else 0, flag), "rve_apply_operator")
         return out
+
+
+class RVEBatch:
+    """A batch of RVEs of uneven grid size (one dimension, precision and nu)."""
+
+    def __init__(self, sizes, precision="mixed", nu=0.3):
+        lib = load()
+        sizes = [tuple(int(v) for v in n) for n in sizes]
+        self.dim = len(sizes[0])
+        self.count = len(sizes)
+        self.sizes = sizes
+        self.ns = 3 if self.dim == 2 else 6
+        flat = (C.c_int64 * (self.count * self.dim))(*[v for n in sizes for v in n])
+        h = C.c_void_p()
+        prec = RVE_MIXED if precision == "mixed" else RVE_FP64
+        _check(lib.rve_batch_create(C.byref(h), self.dim, self.count, flat, prec, float(nu)), "rve_batch_create")
+        self.h = h
+        self.L = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rve_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_material(self, index, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        _check(load().rve_batch_set_material(self.h, int(index), E.ctypes.data_as(C.c_void_p), RVE_F64,
+                                             RVE_PTR_HOST), "rve_batch_set_material")
+
+    def solve(self, E_macro, rel_tol=1e-10, max_iter=5000):
+        Em = np.ascontiguousarray(np.atleast_2d(np.asarray(E_macro, dtype=np.float64)))
+        L = Em.shape[0]
+        info = (rve_info * (self.count * L))()
+        code = load().rve_batch_solve(self.h, Em.ctypes.data_as(C.POINTER(C.c_double)), L, float(rel_tol),
+                                      int(max_iter), info)
+        _check(code, "rve_batch_solve", allow=(RVE_ERR_NOT_CONVERGED,))
+        self.L = L
+        return code, [[info[i * L + l].as_dict() for l in range(L)] for i in range(self.count)]
+
+    def mean_stress(self, index):
+        S = np.zeros((self.L, self.ns))
+        _check(load().rve_batch_mean_stress(self.h, int(index), S.ctypes.data_as(C.POINTER(C.c_double))),
+               "rve_batch_mean_stress")
+        return S
+
+    def effective_tangent(self, index):
+        Cm = np.zeros((self.ns, self.ns))
+        _check(load().rve_batch_effective_tangent(self.h, int(index), Cm.ctypes.data_as(C.POINTER(C.c_double))),
+               "rve_batch_effective_tangent")
+        return Cm

@@ -90,6 +90,7 @@ extern "C" int rve_apply_operator_2d_static(const int64_t* n, const double* leng
   a.N = (int64_t)nx * ny;
   a.kx = nx / 2 + 1;
   a.E = E;
+  a.lcs = 1;
   a.in = p; a.out = q;
   a.spec = spec;
   a.ph[0] = tables; a.ph[1] = tables + kStaticMaxN;

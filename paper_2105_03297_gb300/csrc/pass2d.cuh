@@ -81,7 +81,7 @@ __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int
     } else {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if (a.amode != A_BARE) vloadn<T, VL>(ev[h], a.E + va + h * NX);
+        if (a.amode != A_BARE) vloadn<T, VL>(ev[h], a.E + (int64_t)(l / a.lcs) * N + va + h * NX);
 #pragma unroll
         for (int j = 0; j < GS; ++j) {
           const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + va + h * NX;

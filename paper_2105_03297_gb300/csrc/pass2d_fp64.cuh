@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) residual_2d(Fp64Args a) {
         const int vx = (x - dx) & (a.n[0] - 1), vy = (y - dy) & (a.n[1] - 1);
         double eps[2][3], sig[3];
         strain_2d(u, a.N, a.n[0], a.n[1], vx, vy, em, a.ih[0], a.ih[1], eps);
-        const double e = a.E[(int64_t)vy * a.n[0] + vx];
+        const double e = a.E[(int64_t)(l / a.lcs) * a.N + (int64_t)vy * a.n[0] + vx];
         // shape-function gradients of this node in element 0 / element 1
         double g0x = 0, g0y = 0, g1x = 0, g1y = 0;
         bool in0 = false, in1 = false;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(NT) homogenise_2d(Fp64Args a, double* part, in
     const int x = (int)(v % a.n[0]), y = (int)(v / a.n[0]);
     double eps[2][3], sig[3];
     strain_2d(a.u + (int64_t)l * 2 * a.N, a.N, a.n[0], a.n[1], x, y, a.emac + l * 3, a.ih[0], a.ih[1], eps);
-    const double e = a.E[v];
+    const double e = a.E[(int64_t)(l / a.lcs) * a.N + v];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       stress_2d(eps[q], e, a.lam, a.mu2, sig);
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(NT) energy_2d(Fp64Args a, double* part, int nb
   const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
   const bool ok = v < a.N;
   const int x = ok ? (int)(v % a.n[0]) : 0, y = ok ? (int)(v / a.n[0]) : 0;
-  const double e = ok ? a.E[v] : 0.0;
   int p = 0;
   for (int lb = 0; lb < a.L; ++lb) {
+    const double e = ok ? a.E[(int64_t)(lb / a.lcs) * a.N + v] : 0.0;
     double sb[2][3] = {{0, 0, 0}, {0, 0, 0}};
     if (ok) {
       double eb[2][3];

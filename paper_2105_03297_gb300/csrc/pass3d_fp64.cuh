@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) residual_3d(Fp64Args a) {
     const int vz = (z0 - 1 + ez) & (a.n[2] - 1);
     double eps[6][6];
     strain_3d(u, a.N, a.n, vx, vy, vz, em, a.ih, eps);
-    const double e = a.E[((int64_t)vz * a.n[1] + vy) * a.n[0] + vx];
+    const double e = a.E[(int64_t)(l / a.lcs) * a.N + ((int64_t)vz * a.n[1] + vy) * a.n[0] + vx];
     double f[8][3], fa[8][3];
 #pragma unroll
     for (int c = 0; c < 8; ++c) f[c][0] = f[c][1] = f[c][2] = fa[c][0] = fa[c][1] = fa[c][2] = 0.0;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT) homogenise_3d(Fp64Args a, double* part, in
     const int x = (int)(v % a.n[0]), y = (int)((v / a.n[0]) % a.n[1]), z = (int)(v / ((int64_t)a.n[0] * a.n[1]));
     double eps[6][6], sig[6];
     strain_3d(a.u + (int64_t)l * 3 * a.N, a.N, a.n, x, y, z, a.emac + l * 6, a.ih, eps);
-    const double e = a.E[v];
+    const double e = a.E[(int64_t)(l / a.lcs) * a.N + v];
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       stress_3d(eps[t], e, a.lam, a.mu2, sig);
@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(NT) energy_3d(Fp64Args a, double* part, int nb
   const bool ok = v < a.N;
   const int x = ok ? (int)(v % a.n[0]) : 0, y = ok ? (int)((v / a.n[0]) % a.n[1]) : 0;
   const int z = ok ? (int)(v / ((int64_t)a.n[0] * a.n[1])) : 0;
-  const double e = ok ? a.E[v] : 0.0;
   int p = 0;
   for (int lb = 0; lb < a.L; ++lb) {
+    const double e = ok ? a.E[(int64_t)(lb / a.lcs) * a.N + v] : 0.0;
     double sb[6][6];
     if (ok) {
       double eb[6][6];

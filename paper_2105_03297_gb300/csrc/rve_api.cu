@@ -15,7 +15,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/rve.h"
@@ -33,6 +35,8 @@ struct rve_s {
   int ns = 0, nq = 0, m = 0, D = 0, kx = 0;
   double nu = 0.0, lam = 0.0, mu2 = 0.0;
   bool has_material = false;
+  int lcs = 0;          // > 0: a batch group, slot l uses material l / lcs (rve_batch_*)
+  int n_mat = 1;        // materials held in E64 / Ein
   size_t tsize = 8;  // bytes of the inner precision
   // device memory
   double* E64 = nullptr;
@@ -217,6 +221,7 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   a.dim = h->dim; a.L = L; a.m = h->m; a.ns = h->ns; a.nq = h->nq;
   a.N = h->N; a.kx = h->kx;
   a.E = (const T*)h->Ein;
+  a.lcs = h->lcs > 0 ? h->lcs : L;
   a.x = (T*)h->x; a.r = (T*)h->r; a.p = (T*)h->p;
   a.in = (const T*)h->fbuf; a.out = (T*)h->fbuf;
   a.u64 = u;
@@ -239,6 +244,7 @@ Fp64Args fp64_args(const rve_s* h, int L, const double* u, const double* emac, C
   for (int i = 0; i < 3; ++i) { f.n[i] = h->n[i]; f.ih[i] = (double)h->n[i] / h->len[i]; }
   f.dim = h->dim; f.L = L; f.ns = h->ns; f.nq = h->nq; f.N = h->N;
   f.E = h->E64; f.u = u; f.emac = emac;
+  f.lcs = h->lcs > 0 ? h->lcs : L;
   f.lam = h->lam; f.mu2 = h->mu2;
   f.cg = cg; f.part = h->part; f.part_stride = h->part_stride;
   f.fout = h->fbuf; f.fout_f32 = (h->tsize == 4);
@@ -450,7 +456,93 @@ __global__ void f32_from_f64(const double* in, float* out, int64_t n) {
   if (i < n) out[i] = (float)in[i];
 }
 
+// (Re)allocate the material buffers of a handle for n_mat fields.
+int alloc_materials(rve_s* h, int n_mat) {
+  if (h->Ein && h->Ein != (void*)h->E64) cudaFree(h->Ein);
+  h->Ein = nullptr;
+  free_devp(h->E64);
+  int rc = dev_alloc((void**)&h->E64, (size_t)n_mat * h->N * sizeof(double));
+  if (rc) return rc;
+  if (h->precision == RVE_MIXED) {
+    rc = dev_alloc(&h->Ein, (size_t)n_mat * h->N * sizeof(float));
+    if (rc) return rc;
+  } else {
+    h->Ein = h->E64;
+  }
+  h->n_mat = n_mat;
+  return RVE_OK;
+}
+
+// Validated FP64 copy of a modulus field on the host.
+int read_moduli(int64_t N, const void* E, int E_dtype, int ptr_flags, std::vector<double>& e64) {
+  e64.resize((size_t)N);
+  if (ptr_flags & RVE_PTR_DEVICE) {
+    if (E_dtype == RVE_F64) {
+      CK(cudaMemcpy(e64.data(), E, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> e32((size_t)N);
+      CK(cudaMemcpy(e32.data(), E, (size_t)N * sizeof(float), cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < N; ++i) e64[i] = e32[i];
+    }
+  } else {
+    if (E_dtype == RVE_F64) std::memcpy(e64.data(), E, (size_t)N * sizeof(double));
+    else for (int64_t i = 0; i < N; ++i) e64[i] = ((const float*)E)[i];
+  }
+  for (int64_t i = 0; i < N; ++i)
+    if (!(e64[i] > 0.0) || !std::isfinite(e64[i])) return RVE_ERR_ARG;
+  return RVE_OK;
+}
+
+// Upload field `slot` (FP64 host copy) and its inner-precision copy.
+int upload_material(rve_s* h, int slot, const std::vector<double>& e64) {
+  double* dst = h->E64 + (size_t)slot * h->N;
+  CK(cudaMemcpy(dst, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice));
+  if (h->precision == RVE_MIXED) {
+    f32_from_f64<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(dst, (float*)h->Ein + (size_t)slot * h->N,
+                                                                          h->N);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return RVE_OK;
+}
+
+void set_nu(rve_s* h, double nu) {
+  h->nu = nu;
+  h->lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));  // unit Young's modulus
+  h->mu2 = 1.0 / (1.0 + nu);
+}
+
+// C = S^T M^-T for the L = n_s load cases of one RVE (rows S[l][:]).
+int tangent_from_stress(int ns, const double* S, const double* emac, double* C) {
+  std::vector<double> Minv((size_t)ns * ns);
+  if (!invert(ns, emac, Minv.data())) return RVE_ERR_ARG;
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < ns; ++t) {
+      double v = 0.0;
+      for (int l = 0; l < ns; ++l) v += S[(size_t)l * ns + s] * Minv[(size_t)t * ns + l];
+      C[s * ns + t] = v;
+    }
+  return RVE_OK;
+}
+
 }  // namespace
+
+struct rve_batch_s {
+  int dim = 0, count = 0, precision = RVE_FP64;
+  double nu = 0.3;
+  struct Group {
+    int n[3] = {1, 1, 1};
+    std::vector<int> members;   // RVE indices
+    std::vector<char> has_mat;
+    rve_s* h = nullptr;
+    cudaStream_t stream = nullptr;
+  };
+  std::vector<Group> groups;
+  std::vector<int> group_of, slot_of;
+  int L = 0;
+  bool solved = false;
+  std::vector<double> emac;     // [L][ns]
+};
 
 // ====================================================================
 extern "C" {
@@ -753,6 +845,146 @@ int rve_timing_read(rve_t h, double* ms, int64_t* launches) {
     h->t_cnt[k] = 0;
   }
   return RVE_OK;
+}
+
+int rve_batch_destroy(rve_batch_t b) {
+  if (!b) return RVE_OK;
+  for (auto& g : b->groups) {
+    if (g.h) rve_destroy(g.h);
+    if (g.stream) cudaStreamDestroy(g.stream);
+  }
+  delete b;
+  return RVE_OK;
+}
+
+int rve_batch_create(rve_batch_t* out, int dim, int count, const int64_t* n, int precision, double nu) {
+  if (!out || !n || count < 1 || (dim != 2 && dim != 3)) return RVE_ERR_ARG;
+  if (!(nu > -1.0 && nu < 0.5)) return RVE_ERR_ARG;
+  *out = nullptr;
+  rve_batch_s* b = new (std::nothrow) rve_batch_s();
+  if (!b) return RVE_ERR_OOM;
+  b->dim = dim; b->count = count; b->precision = precision; b->nu = nu;
+  b->group_of.assign(count, -1);
+  b->slot_of.assign(count, -1);
+  std::map<std::vector<int64_t>, int> index;
+  for (int i = 0; i < count; ++i) {
+    std::vector<int64_t> key(n + (size_t)i * dim, n + (size_t)(i + 1) * dim);
+    auto it = index.find(key);
+    int gi;
+    if (it == index.end()) {
+      gi = (int)b->groups.size();
+      index[key] = gi;
+      b->groups.emplace_back();
+      for (int a = 0; a < dim; ++a) b->groups[gi].n[a] = (int)key[a];
+    } else {
+      gi = it->second;
+    }
+    b->group_of[i] = gi;
+    b->slot_of[i] = (int)b->groups[gi].members.size();
+    b->groups[gi].members.push_back(i);
+  }
+  for (auto& g : b->groups) {
+    g.has_mat.assign(g.members.size(), 0);
+    if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError(); rve_batch_destroy(b); return RVE_ERR_CUDA;
+    }
+    int64_t nn[3] = {g.n[0], g.n[1], g.n[2]};
+    int rc = rve_create(&g.h, dim, nn, nullptr, precision, g.stream);
+    if (!rc) rc = alloc_materials(g.h, (int)g.members.size());
+    if (rc) { rve_batch_destroy(b); return rc; }
+    set_nu(g.h, nu);
+  }
+  *out = b;
+  return RVE_OK;
+}
+
+int rve_batch_set_material(rve_batch_t b, int index, const void* E, int E_dtype, int ptr_flags) {
+  if (!b || !E || index < 0 || index >= b->count || (E_dtype != RVE_F32 && E_dtype != RVE_F64)) return RVE_ERR_ARG;
+  auto& g = b->groups[b->group_of[index]];
+  std::vector<double> e64;
+  int rc = read_moduli(g.h->N, E, E_dtype, ptr_flags, e64);
+  if (rc) return rc;
+  rc = upload_material(g.h, b->slot_of[index], e64);
+  if (rc) return rc;
+  g.has_mat[b->slot_of[index]] = 1;
+  b->solved = false;
+  return RVE_OK;
+}
+
+int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info) {
+  if (!b || !E_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_iter < 1) return RVE_ERR_ARG;
+  const int ns = b->dim == 2 ? 3 : 6;
+  for (int i = 0; i < L * ns; ++i) if (!std::isfinite(E_macro[i])) return RVE_ERR_ARG;
+  for (auto& g : b->groups)
+    for (char c : g.has_mat) if (!c) return RVE_ERR_ARG;
+  b->solved = false;
+  const int G = (int)b->groups.size();
+  std::vector<int> codes(G, RVE_OK);
+  std::vector<std::vector<rve_info>> infos(G);
+  // one host thread per group: the groups' launches overlap on their streams
+  auto run = [&](int gi) {
+    auto& g = b->groups[gi];
+    rve_s* h = g.h;
+    const int Lg = (int)g.members.size() * L;
+    std::vector<double> em((size_t)Lg * ns);
+    for (int s = 0; s < Lg; ++s)
+      for (int c = 0; c < ns; ++c) em[(size_t)s * ns + c] = E_macro[(size_t)(s % L) * ns + c];
+    h->lcs = L;
+    h->has_material = true;
+    h->solved = false;
+    int rc = ensure_capacity(h, Lg);
+    if (rc) { codes[gi] = rc; return; }
+    infos[gi].resize(Lg);
+    const int st = (h->precision == RVE_MIXED)
+                       ? solve_impl<float>(h, em.data(), Lg, rel_tol, max_iter, infos[gi].data(), h->u, h->emac_d)
+                       : solve_impl<double>(h, em.data(), Lg, rel_tol, max_iter, infos[gi].data(), h->u, h->emac_d);
+    if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED && st != RVE_ERR_NONFINITE) { codes[gi] = st; return; }
+    h->emac_h = em;
+    h->L_solved = Lg;
+    rc = compute_mean_stress(h, Lg);
+    if (rc) { codes[gi] = rc; return; }
+    h->solved = true;
+    codes[gi] = st;
+  };
+  if (G == 1) {
+    run(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int gi = 0; gi < G; ++gi) th.emplace_back(run, gi);
+    for (auto& t : th) t.join();
+  }
+  int worst = RVE_OK;
+  for (int gi = 0; gi < G; ++gi) {
+    const int c = codes[gi];
+    if (c != RVE_OK && c != RVE_ERR_NOT_CONVERGED && c != RVE_ERR_NONFINITE) return c;
+    if (c == RVE_ERR_NONFINITE || (c != RVE_OK && worst == RVE_OK)) worst = c;
+  }
+  if (info)
+    for (int i = 0; i < b->count; ++i) {
+      const auto& ig = infos[b->group_of[i]];
+      for (int l = 0; l < L; ++l) info[(size_t)i * L + l] = ig[(size_t)b->slot_of[i] * L + l];
+    }
+  b->L = L;
+  b->emac.assign(E_macro, E_macro + (size_t)L * ns);
+  b->solved = true;
+  return worst;
+}
+
+int rve_batch_mean_stress(rve_batch_t b, int index, double* S) {
+  if (!b || !S || !b->solved || index < 0 || index >= b->count) return RVE_ERR_ARG;
+  const int ns = b->dim == 2 ? 3 : 6;
+  const auto& g = b->groups[b->group_of[index]];
+  std::memcpy(S, g.h->S_h.data() + (size_t)b->slot_of[index] * b->L * ns, (size_t)b->L * ns * sizeof(double));
+  return RVE_OK;
+}
+
+int rve_batch_effective_tangent(rve_batch_t b, int index, double* C) {
+  const int ns = b ? (b->dim == 2 ? 3 : 6) : 0;
+  if (!b || !C || !b->solved || b->L != ns) return RVE_ERR_ARG;
+  std::vector<double> S((size_t)ns * ns);
+  int rc = rve_batch_mean_stress(b, index, S.data());
+  if (rc) return rc;
+  return tangent_from_stress(ns, S.data(), b->emac.data(), C);
 }
 
 }  // extern "C"

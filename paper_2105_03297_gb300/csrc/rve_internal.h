@@ -36,7 +36,8 @@ template <typename T> struct PassArgs {
   int dim, L, m, ns, nq;
   int64_t N;         // voxels
   int kx;            // n_x/2 + 1
-  const T* E;        // [N] Young's modulus
+  const T* E;        // [L / lcs][N] Young's modulus (one field per material)
+  int lcs;           // load-case slots per material: slot l uses field l / lcs
   T* x; T* r; T* p;  // [L][m][N] CG vectors
   const T* in;       // [L][m or D][N] input field (A_FIELD / A_BARE / A_NODAL)
   T* out;            // [L][m][N] output field (E_OUT)
@@ -63,7 +64,8 @@ struct Fp64Args {
   int n[3];
   int dim, L, ns, nq;
   int64_t N;
-  const double* E;      // [N]
+  const double* E;      // [L / lcs][N]
+  int lcs;              // load-case slots per material (slot l uses field l / lcs)
   const double* u;      // [L][D][N] nodal fluctuation displacement
   const double* emac;   // [L][ns]
   double ih[3], lam, mu2;

@@ -1,0 +1,68 @@
+"""Batches of RVEs of uneven grid size (rve_batch_*) against the FP64 oracle.
+
+Every RVE of the batch must give the C_eff of its own oracle solve to 1e-9,
+whatever the grid sizes of the other RVEs (slots of one size group share
+launches but keep their own CG scalars and stop on their own).
+"""
+import numpy as np
+import pytest
+
+from oracle.fe_projection import Problem
+from tests.gpu_util import lognormal, rel_max, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uneven_2d_batch(prec):
+    from paper_2105_03297_gb300 import RVEBatch
+    sizes = [(32, 32), (64, 32), (32, 32), (16, 64), (64, 32), (32, 32)]
+    fields = [lognormal(n, 100 + i, sigma=1.2) for i, n in enumerate(sizes)]
+    refs = [Problem(n, E, 0.3).effective_tangent(np.eye(3), tol=1e-13)[0] for n, E in zip(sizes, fields)]
+    with RVEBatch(sizes, precision=prec, nu=0.3) as b:
+        for i, E in enumerate(fields):
+            b.set_material(i, E)
+        code, info = b.solve(np.eye(3), rel_tol=1e-12, max_iter=4000)
+        assert code == 0, info
+        for i in range(len(sizes)):
+            assert rel_max(b.effective_tangent(i), refs[i]) < 1e-9, i
+            S = b.mean_stress(i)
+            assert rel_max(S.T, refs[i]) < 1e-9
+
+
+def test_uneven_3d_batch_mixed():
+    from paper_2105_03297_gb300 import RVEBatch
+    sizes = [(16, 16, 16), (32, 16, 16), (16, 16, 16)]
+    fields = [lognormal(n, 200 + i) for i, n in enumerate(sizes)]
+    refs = [Problem(n, E, 0.3).effective_tangent(np.eye(6), tol=1e-13)[0] for n, E in zip(sizes, fields)]
+    with RVEBatch(sizes, precision="mixed", nu=0.3) as b:
+        for i, E in enumerate(fields):
+            b.set_material(i, E)
+        code, info = b.solve(np.eye(6), rel_tol=1e-12, max_iter=4000)
+        assert code == 0, info
+        for i in range(len(sizes)):
+            assert rel_max(b.effective_tangent(i), refs[i]) < 1e-9, i
+
+
+def test_batch_matches_single_solves():
+    """A batch slot and a single-RVE handle run the same kernels: same result."""
+    from paper_2105_03297_gb300 import RVE, RVEBatch
+    sizes = [(64, 64), (128, 128)]
+    fields = [lognormal(n, 300 + i, sigma=1.5) for i, n in enumerate(sizes)]
+    singles = []
+    for n, E in zip(sizes, fields):
+        with RVE(n, precision="mixed") as r:
+            r.set_material(E, 0.3)
+            r.solve(np.eye(3), rel_tol=1e-11, max_iter=4000)
+            singles.append(r.effective_tangent())
+    with RVEBatch(sizes, precision="mixed", nu=0.3) as b:
+        for i, E in enumerate(fields):
+            b.set_material(i, E)
+        b.solve(np.eye(3), rel_tol=1e-11, max_iter=4000)
+        for i in range(2):
+            assert rel_max(b.effective_tangent(i), singles[i]) < 1e-10
