@@ -37,10 +37,11 @@
  *  - A handle owns all of its device memory; caller buffers are borrowed for
  *    the duration of a call only.  Pointers flagged RVE_PTR_DEVICE are device
  *    pointers on the handle's device, otherwise host pointers.
- *  - All work is enqueued on the CUDA stream given to rve_create (0 = the
- *    legacy default stream).  Calls returning results to host memory
- *    synchronise that stream before returning.  A handle must not be used by
- *    two host threads at once.
+ *  - Work runs on a stream the handle creates; at every call it is ordered
+ *    after the work already queued on the stream given to rve_create (NULL =
+ *    the legacy default stream), and calls return when their results are
+ *    ready (host or device).  A handle must not be used by two host threads
+ *    at once.  The CG iterations run as CUDA graphs of 8 iterations.
  *
  * Errors: every function returns RVE_OK (0) or a negative code; the text of a
  * code is rve_error_string(code).  After RVE_ERR_CUDA the handle should be

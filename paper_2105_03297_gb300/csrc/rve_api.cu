@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <new>
 #include <thread>
 #include <vector>
@@ -30,7 +31,9 @@ struct rve_s {
   int64_t N = 0;
   double len[3] = {1, 1, 1};
   int precision = RVE_FP64;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // internal stream all work runs on
+  cudaStream_t user_stream = nullptr;  // caller's stream (ordered before every call's work)
+  cudaEvent_t join_ev = nullptr;
   int device = 0;
   int ns = 0, nq = 0, m = 0, D = 0, kx = 0;
   double nu = 0.0, lam = 0.0, mu2 = 0.0;
@@ -69,6 +72,8 @@ struct rve_s {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   double t_ms[RVE_NKINDS] = {0};
   int64_t t_cnt[RVE_NKINDS] = {0};
+  std::vector<Rec>* capturing = nullptr;  // event pairs recorded while capturing a graph
+  CgState* cg_h2 = nullptr;               // second pinned copy of the CG state (run-ahead)
 };
 
 namespace {
@@ -95,24 +100,47 @@ template <typename F> cudaError_t timed(rve_s* h, int kind, F fn) {
     cudaEventCreate(&ev.first);
     cudaEventCreate(&ev.second);
   }
-  cudaEventRecord(ev.first, h->stream);
-  cudaError_t e = fn();
-  cudaEventRecord(ev.second, h->stream);
-  h->pending.push_back({kind, ev.first, ev.second});
+  // inside a graph capture the events must become event-record nodes
+  const unsigned flags = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaError_t e = cudaEventRecordWithFlags(ev.first, h->stream, flags);
+  if (e == cudaSuccess) e = fn();
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev.second, h->stream, flags);
+  if (h->capturing) h->capturing->push_back({kind, ev.first, ev.second});
+  else h->pending.push_back({kind, ev.first, ev.second});
   return e;
 }
 
-// Accumulate the elapsed times of completed launches (stream synchronised).
+// Order the handle's stream after everything already queued on the caller's stream.
+int join_user(rve_s* h) {
+  if (h->user_stream == h->stream) return RVE_OK;
+  if (cudaEventRecord(h->join_ev, h->user_stream) != cudaSuccess ||
+      cudaStreamWaitEvent(h->stream, h->join_ev, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return RVE_ERR_CUDA;
+  }
+  return RVE_OK;
+}
+
+// Accumulate the elapsed times of the launches that have completed; the
+// others stay pending.
 void flush_timing(rve_s* h) {
+  std::vector<rve_s::Rec> keep;
   for (auto& r : h->pending) {
+    if (cudaEventQuery(r.b) != cudaSuccess) {
+      cudaGetLastError();
+      keep.push_back(r);
+      continue;
+    }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       h->t_ms[r.kind] += ms;
       h->t_cnt[r.kind] += 1;
+    } else {
+      cudaGetLastError();
     }
     h->ev_pool.push_back({r.a, r.b});
   }
-  h->pending.clear();
+  h->pending.swap(keep);
 }
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -161,6 +189,7 @@ void free_L(rve_s* h) {
   free_devp(h->u); free_devp(h->uadj); free_devp(h->part); free_devp(h->cg);
   free_devp(h->emac_d); free_devp(h->emac_adj_d);
   if (h->cg_h) { cudaFreeHost(h->cg_h); h->cg_h = nullptr; }
+  if (h->cg_h2) { cudaFreeHost(h->cg_h2); h->cg_h2 = nullptr; }
   h->Lcap = 0;
 }
 
@@ -199,7 +228,8 @@ int ensure_capacity(rve_s* h, int L) {
       (rc = dev_alloc((void**)&h->emac_d, (size_t)Lp * h->ns * sizeof(double))) ||
       (rc = dev_alloc((void**)&h->emac_adj_d, (size_t)h->ns * h->ns * sizeof(double))))
     { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
-  if (cudaMallocHost((void**)&h->cg_h, (size_t)Lp * sizeof(CgState)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&h->cg_h, (size_t)Lp * sizeof(CgState)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->cg_h2, (size_t)Lp * sizeof(CgState)) != cudaSuccess) {
     cudaGetLastError(); free_L(h); if (keep_u) cudaFree(keep_u); return RVE_ERR_OOM;
   }
   cudaMemset(h->p, 0, fld);
@@ -290,6 +320,110 @@ int write_state(rve_s* h, int L) {
   return RVE_OK;
 }
 
+// The projected-CG loop in batches of K iterations.  Each batch is a CUDA
+// graph of K x (passes A, [B,] C, [D,] E); two copies (each with its own
+// timing events) are launched alternately, and the host checks the CG state
+// copied after batch i while batch i+1 already runs, so the GPU does not wait
+// for the host.  A batch launched after every slot has stopped costs only the
+// early exits of its kernels.  Without graphs (capture not possible, e.g. on
+// the legacy default stream) the same launches are issued directly.
+template <typename T> struct CgRunner {
+  rve_s* h;
+  int L, K;
+  PassArgs<T> a;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<rve_s::Rec> recs[2];
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  CgState* host[2];
+
+  CgRunner(rve_s* h_, int L_, const PassArgs<T>& a_, int K_) : h(h_), L(L_), K(K_), a(a_) {
+    host[0] = h->cg_h;
+    host[1] = h->cg_h2;
+    for (int b = 0; b < 2; ++b) cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+    for (int b = 0; b < 2; ++b) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      h->capturing = &recs[b];
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = apply_passes<T>(h, a);
+      h->capturing = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess || !g || cudaGraphInstantiate(&exec[b], g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        exec[b] = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+      if (!exec[b]) break;
+    }
+    if (!exec[0] || !exec[1]) {
+      for (int b = 0; b < 2; ++b) {
+        if (exec[b]) cudaGraphExecDestroy(exec[b]);
+        exec[b] = nullptr;
+        for (auto& r : recs[b]) h->ev_pool.push_back({r.a, r.b});
+        recs[b].clear();
+      }
+    }
+  }
+  ~CgRunner() {
+    for (int b = 0; b < 2; ++b) {
+      if (exec[b]) cudaGraphExecDestroy(exec[b]);
+      if (copied[b]) cudaEventDestroy(copied[b]);
+      for (auto& r : recs[b]) h->ev_pool.push_back({r.a, r.b});
+    }
+  }
+  cudaError_t launch(int b) {
+    cudaError_t e = cudaSuccess;
+    if (exec[b]) {
+      e = cudaGraphLaunch(exec[b], h->stream);
+    } else {
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = apply_passes<T>(h, a);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host[b], h->cg, (size_t)L * sizeof(CgState), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[b], h->stream);
+    return e;
+  }
+  // Wait for batch b's state copy; account its kernel times.
+  cudaError_t wait(int b) {
+    cudaError_t e = cudaEventSynchronize(copied[b]);
+    if (e == cudaSuccess && h->timing && exec[b]) {
+      for (auto& r : recs[b]) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+          h->t_ms[r.kind] += ms;
+          h->t_cnt[r.kind] += 1;
+        }
+      }
+    }
+    if (e == cudaSuccess && h->timing && !exec[b]) flush_timing(h);
+    return e;
+  }
+  // Run batches until no active slot is still iterating (or max_batches).
+  int run(const std::vector<int>& active, int max_batches) {
+    int cur = 0;
+    if (cudaError_t e = launch(cur)) return map_err(e);
+    for (int n = 1;; ++n) {
+      const bool ahead = n < max_batches;
+      if (ahead) {
+        if (cudaError_t e = launch(1 - cur)) return map_err(e);
+      }
+      if (cudaError_t e = wait(cur)) return map_err(e);
+      bool running = false;
+      for (int l = 0; l < L; ++l)
+        if (active[l] && host[cur][l].status == ST_RUN) running = true;
+      if (!running || !ahead) {
+        if (ahead) {
+          if (cudaError_t e = wait(1 - cur)) return map_err(e);
+        }
+        return RVE_OK;
+      }
+      cur = 1 - cur;
+    }
+  }
+};
+
 // The solve driver.  u_out [L][D][N] receives the FP64 nodal fluctuation.
 template <typename T>
 int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max_iter, rve_info* info,
@@ -309,6 +443,7 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
   Fp64Args fa = fp64_args(h, L, u_out, emac_dev, h->cg);
   PassArgs<T> a = pass_args<T>(h, L, u_out, emac_dev);
   const int check_every = 8;
+  std::unique_ptr<CgRunner<T>> runner;  // built at the first inner solve, reused by later ones
 
   for (int step = 0;; ++step) {
     // FP64 residual of the current iterate
@@ -354,14 +489,8 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
     CK(apply_passes<T>(h, a));
     // projected CG
     a.cgphase = 1; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
-    for (int it = 0; it < max_iter; it += check_every) {
-      for (int k = 0; k < check_every; ++k) CK(apply_passes<T>(h, a));
-      if ((rc = read_state(h, L))) return rc;
-      bool running = false;
-      for (int l = 0; l < L; ++l)
-        if (active[l] && h->cg_h[l].status == ST_RUN) running = true;
-      if (!running) break;
-    }
+    if (!runner) runner.reset(new CgRunner<T>(h, L, a, check_every));
+    if ((rc = runner->run(active, (max_iter + check_every - 1) / check_every + 1))) return rc;
     // apply the x update the last iteration deferred
     CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<T>(a, h->stream); }));
     if ((rc = read_state(h, L))) return rc;
@@ -576,7 +705,14 @@ int rve_create(rve_t* out, int dim, const int64_t* n, const double* length, int 
   h->N = 1;
   for (int a = 0; a < dim; ++a) { h->n[a] = (int)n[a]; h->N *= n[a]; h->len[a] = length ? length[a] : 1.0; }
   h->precision = precision;
-  h->stream = (cudaStream_t)cuda_stream;
+  h->user_stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return RVE_ERR_CUDA;
+  }
   h->ns = dim == 2 ? 3 : 6;
   h->nq = dim == 2 ? 2 : 6;
   h->m = h->ns * h->nq;
@@ -606,6 +742,8 @@ int rve_destroy(rve_t h) {
   free_devp(h->E64);
   free_devp(h->hpart);
   for (int a = 0; a < 3; ++a) { free_dev(h->ph[a]); free_dev(h->tw[a]); }
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
+  if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return RVE_OK;
 }
@@ -622,6 +760,8 @@ int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim) {
 int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_flags) {
   if (!h || !E || (E_dtype != RVE_F32 && E_dtype != RVE_F64)) return RVE_ERR_ARG;
   if (!(nu > -1.0 && nu < 0.5)) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
+  if (ptr_flags & RVE_PTR_DEVICE) CK(cudaStreamSynchronize(h->stream));
   std::vector<double> e64((size_t)h->N);
   if (ptr_flags & RVE_PTR_DEVICE) {
     if (E_dtype == RVE_F64) {
@@ -654,6 +794,7 @@ int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_fla
 int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info) {
   if (!h || !E_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_iter < 1) return RVE_ERR_ARG;
   if (!h->has_material) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
   for (int i = 0; i < L * h->ns; ++i) if (!std::isfinite(E_macro[i])) return RVE_ERR_ARG;
   h->solved = false;
   int rc = ensure_capacity(h, L);
@@ -693,6 +834,7 @@ int rve_effective_tangent(rve_t h, double* C) {
 
 int rve_energy_tangent(rve_t h, double* Ce) {
   if (!h || !Ce || !h->solved) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
   const int L = h->L_solved;
   const int npair = L * (L + 1) / 2;
   Fp64Args fa = fp64_args(h, L, h->u, h->emac_d, h->cg);
@@ -723,6 +865,7 @@ int rve_energy_tangent(rve_t h, double* Ce) {
 
 int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
   if (!h || !eps || !h->solved || load_case < 0 || load_case >= h->L_solved) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
   Fp64Args fa = fp64_args(h, h->L_solved, h->u, h->emac_d, h->cg);
   const size_t bytes = (size_t)h->m * h->N * sizeof(double);
   double* dst = (double*)eps;
@@ -742,6 +885,7 @@ int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
 int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter, void* grad_E, int ptr_flags) {
   if (!h || !W || !grad_E || !h->solved || h->L_solved != h->ns || !(rel_tol > 0.0) || max_iter < 1)
     return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
   const int ns = h->ns, L = h->L_solved;
   std::vector<double> Minv((size_t)ns * ns), Wp((size_t)ns * L, 0.0);
   if (!invert(ns, h->emac_h.data(), Minv.data())) return RVE_ERR_ARG;
@@ -801,6 +945,7 @@ int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter, void* gr
 int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int ptr_flags) {
   if (!h || !p || !q) return RVE_ERR_ARG;
   if (apply_material && !h->has_material) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
   const size_t bytes = (size_t)h->m * h->N * h->tsize;
   const cudaMemcpyKind kin = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
