@@ -370,6 +370,7 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": None, "kernel": dom,
                      "peak_source": peak_kind},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant"), r.schedule()[0])),
         "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(E_host.nbytes + Em.nbytes),
                 "d2h_bytes_per_step": int(C_h.nbytes)},
         "gpu_launches": launches,

@@ -152,6 +152,15 @@ int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags);
  * material step is skipped and q = G * p (the bare projection). */
 int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int ptr_flags);
 
+/* Schedule of the FFT passes (tile shapes).  variants[0] / variants[1] are the
+ * rows-per-block variants of the first (material + x FFT) and last (inverse x
+ * FFT + CG update) pass: 0 default, 1 half, 2 double, -1 = choose by timing
+ * the candidates on the handle's buffers at the next solve (the default; the
+ * choice is cached per grid and precision).  rve_schedule also returns the
+ * measured candidate times candidate_ms[2][3] (may be NULL). */
+int rve_schedule(rve_t h, int* variants, float* candidate_ms);
+int rve_set_schedule(rve_t h, const int* variants);
+
 /* Measurement hooks (not part of the method).  With timing enabled, every
  * kernel launch of the solver is bracketed by CUDA events on the handle's
  * stream; rve_timing_read returns, per kernel kind, the summed device time in

@@ -51,6 +51,8 @@ SIGNATURES = {
     "rve_adjoint": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int, C.c_void_p, C.c_int]),
     "rve_get_strain": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "rve_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "rve_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "rve_timing_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "rve_apply_operator_2d_static": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_void_p,
@@ -207,6 +209,17 @@ class RVE:
         p, flag, _keep = _dptr(out)
         _check(load().rve_get_strain(self.h, int(load_case), p, flag), "rve_get_strain")
         return out
+
+    def schedule(self):
+        """(variants of passes A and E, candidate times [2][3] in ms)."""
+        v = (C.c_int * 2)()
+        t = (C.c_float * 6)()
+        _check(load().rve_schedule(self.h, v, t), "rve_schedule")
+        return [v[0], v[1]], [[t[0], t[1], t[2]], [t[3], t[4], t[5]]]
+
+    def set_schedule(self, var_a, var_e):
+        v = (C.c_int * 2)(int(var_a), int(var_e))
+        _check(load().rve_set_schedule(self.h, v), "rve_set_schedule")
 
     KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other")
 

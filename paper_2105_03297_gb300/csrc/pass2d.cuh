@@ -188,7 +188,7 @@ __device__ __forceinline__ void pass_a_store(const cplx<T>* buf, int gs, cplx<T>
 // grid (n_y/TY, groups, L), groups = n_q element blocks (n_s components each)
 // or one block of D nodal components (A_NODAL).
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_a_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pass_a_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 3;
@@ -426,7 +426,7 @@ struct PassEStore {
 // grid (n_y/TY, groups, L): groups = n_q elements (3 components each) or one
 // group of the D = 2 nodal components (E_NODAL); inverse real FFT along x.
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pass_e_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
@@ -501,9 +501,14 @@ template <typename T> struct Tile2D;
 template <> struct Tile2D<float> { static constexpr int TY = 8; };
 template <> struct Tile2D<double> { static constexpr int TY = 4; };
 
-template <typename T, int NX>
-cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile2D<T>::TY;
+// Tile variants: rows per block TY = default, half, double (the autotuner
+// times them on the live buffers and keeps the fastest).
+template <typename T> constexpr int tile_rows(int v) {
+  return v == 1 ? Tile2D<T>::TY / 2 : v == 2 ? Tile2D<T>::TY * 2 : Tile2D<T>::TY;
+}
+
+template <typename T, int NX, int TY>
+cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_2d<T, NX, TY, NT>;
@@ -513,9 +518,8 @@ cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
-template <typename T, int NX>
-cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile2D<T>::TY;
+template <typename T, int NX, int TY>
+cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_2d<T, NX, TY, NT>;
@@ -524,6 +528,22 @@ cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   dim3 grid(a.n[1] / TY, a.emode == E_NODAL ? 1 : 2, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T, int NX>
+cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (NX >= 64) {
+    if (a.var_a == 1) return launch_a_2d_t<T, NX, tile_rows<T>(1)>(a, s);
+    if (a.var_a == 2 && a.n[1] >= tile_rows<T>(2)) return launch_a_2d_t<T, NX, tile_rows<T>(2)>(a, s);
+  }
+  return launch_a_2d_t<T, NX, tile_rows<T>(0)>(a, s);
+}
+template <typename T, int NX>
+cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (NX >= 64) {
+    if (a.var_e == 1) return launch_e_2d_t<T, NX, tile_rows<T>(1)>(a, s);
+    if (a.var_e == 2 && a.n[1] >= tile_rows<T>(2)) return launch_e_2d_t<T, NX, tile_rows<T>(2)>(a, s);
+  }
+  return launch_e_2d_t<T, NX, tile_rows<T>(0)>(a, s);
 }
 template <typename T, int NY>
 cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {

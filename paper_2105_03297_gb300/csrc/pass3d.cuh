@@ -29,7 +29,7 @@ __host__ __device__ constexpr int kuhn_perm(int t, int i) {
 // ---------------------------------------------------------------- pass A
 // grid (n_y/TY, n_z, L*G), G = 6 tetrahedra (6 components each) or 1 (nodal, 3).
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_a_3d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pass_a_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 6;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
 // grid (n_y/TY, n_z, L*G): G = 6 tetrahedra (6 components each) or one group
 // of the 3 nodal components (E_NODAL); inverse real FFT along x and update.
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_e_3d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pass_e_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
@@ -282,9 +282,12 @@ template <typename T> struct Tile3D;
 template <> struct Tile3D<float> { static constexpr int TY = 8; static constexpr int TZB = 16; };
 template <> struct Tile3D<double> { static constexpr int TY = 4; static constexpr int TZB = 8; };
 
-template <typename T, int NX>
-cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile3D<T>::TY;
+template <typename T> constexpr int tile_rows3(int v) {
+  return v == 1 ? Tile3D<T>::TY / 2 : v == 2 ? Tile3D<T>::TY * 2 : Tile3D<T>::TY;
+}
+
+template <typename T, int NX, int TY>
+cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_3d<T, NX, TY, NT>;
@@ -294,9 +297,8 @@ cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
-template <typename T, int NX>
-cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int TY = Tile3D<T>::TY;
+template <typename T, int NX, int TY>
+cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_3d<T, NX, TY, NT>;
@@ -305,6 +307,22 @@ cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.emode == E_NODAL ? 1 : 6));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T, int NX>
+cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (NX >= 64) {
+    if (a.var_a == 1) return launch_a_3d_t<T, NX, tile_rows3<T>(1)>(a, s);
+    if (a.var_a == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_a_3d_t<T, NX, tile_rows3<T>(2)>(a, s);
+  }
+  return launch_a_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
+}
+template <typename T, int NX>
+cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (NX >= 64) {
+    if (a.var_e == 1) return launch_e_3d_t<T, NX, tile_rows3<T>(1)>(a, s);
+    if (a.var_e == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_e_3d_t<T, NX, tile_rows3<T>(2)>(a, s);
+  }
+  return launch_e_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
 }
 template <typename T, int NY, bool FWD>
 cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {

@@ -17,6 +17,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <thread>
 #include <vector>
@@ -74,6 +76,8 @@ struct rve_s {
   int64_t t_cnt[RVE_NKINDS] = {0};
   std::vector<Rec>* capturing = nullptr;  // event pairs recorded while capturing a graph
   CgState* cg_h2 = nullptr;               // second pinned copy of the CG state (run-ahead)
+  int var[2] = {-1, -1};                  // tile variants of passes A and E (-1 = autotune at first solve)
+  float tune_ms[2][3] = {{0}};            // measured times of the candidates (last tuning)
 };
 
 namespace {
@@ -265,6 +269,8 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   a.lam = (T)h->lam; a.mu2 = (T)h->mu2;
   a.inv_n = (T)(1.0 / (double)h->N);
   a.cg = h->cg; a.part = h->part; a.part_stride = h->part_stride;
+  a.var_a = h->var[0] < 0 ? 0 : h->var[0];
+  a.var_e = h->var[1] < 0 ? 0 : h->var[1];
   return a;
 }
 
@@ -317,6 +323,75 @@ int read_state(rve_s* h, int L) {
 int write_state(rve_s* h, int L) {
   CK(cudaMemcpyAsync(h->cg, h->cg_h, (size_t)L * sizeof(CgState), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+// ---- autotuner: tile variants of passes A and E ------------------------
+// Candidates: rows per block = default, half, double.  Each is timed on the
+// handle's own buffers (operator-application modes on a zeroed field, 2 warm-up
+// and 3 timed launches, CUDA events on the handle's stream) and the fastest is
+// kept; choices are cached per (dimension, grid, precision) for the process.
+struct TuneKey {
+  int dim, n0, n1, n2, tsize;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dim, n0, n1, n2, tsize) < std::tie(o.dim, o.n0, o.n1, o.n2, o.tsize);
+  }
+};
+std::map<TuneKey, std::pair<int, int>> g_tuned;
+std::mutex g_tune_mutex;
+
+template <typename T> int autotune(rve_s* h) {
+  const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], (int)h->tsize};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      if (h->var[0] < 0) h->var[0] = it->second.first;
+      if (h->var[1] < 0) h->var[1] = it->second.second;
+      return RVE_OK;
+    }
+  }
+  const size_t fld = (size_t)h->m * h->N * h->tsize;
+  CK(cudaMemsetAsync(h->fbuf, 0, fld, h->stream));
+  std::memset(h->cg_h, 0, sizeof(CgState));
+  h->cg_h[0].active = 1;
+  int rc = write_state(h, 1);
+  if (rc) return rc;
+  PassArgs<T> a = pass_args<T>(h, 1, h->u, h->emac_d);
+  a.cgphase = 0; a.amode = A_FIELD; a.pmode = P_G; a.emode = E_OUT;
+  a.in = (const T*)h->fbuf; a.out = (T*)h->x;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best[2] = {0, 0};
+  for (int which = 0; which < 2; ++which) {
+    float best_ms = 1e30f;
+    for (int v = 0; v < 3; ++v) {
+      a.var_a = which == 0 ? v : best[0];
+      a.var_e = which == 1 ? v : 0;
+      auto one = [&]() -> cudaError_t {
+        if (which == 0) return h->dim == 2 ? launch_pass_a_2d<T>(a, h->stream) : launch_pass_a_3d<T>(a, h->stream);
+        return h->dim == 2 ? launch_pass_e_2d<T>(a, h->stream) : launch_pass_e_3d<T>(a, h->stream);
+      };
+      // pass E reads the x-spectrum: let pass A fill it first
+      if (which == 1) CK(h->dim == 2 ? launch_pass_a_2d<T>(a, h->stream) : launch_pass_a_3d<T>(a, h->stream));
+      for (int k = 0; k < 2; ++k) CK(one());
+      CK(cudaEventRecord(e0, h->stream));
+      for (int k = 0; k < 3; ++k) CK(one());
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      h->tune_ms[which][v] = ms / 3.0f;
+      if (ms < best_ms) { best_ms = ms; best[which] = v; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (h->var[0] < 0) h->var[0] = best[0];
+  if (h->var[1] < 0) h->var[1] = best[1];
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tuned[key] = {best[0], best[1]};
   return RVE_OK;
 }
 
@@ -799,6 +874,10 @@ int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_ite
   h->solved = false;
   int rc = ensure_capacity(h, L);
   if (rc) return rc;
+  if (h->var[0] < 0 || h->var[1] < 0) {
+    rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
+    if (rc) return rc;
+  }
   const int st = (h->precision == RVE_MIXED)
                      ? solve_impl<float>(h, E_macro, L, rel_tol, max_iter, info, h->u, h->emac_d)
                      : solve_impl<double>(h, E_macro, L, rel_tol, max_iter, info, h->u, h->emac_d);
@@ -971,6 +1050,25 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
   return RVE_OK;
 }
 
+int rve_schedule(rve_t h, int* variants, float* candidate_ms) {
+  if (!h || !variants) return RVE_ERR_ARG;
+  variants[0] = h->var[0];
+  variants[1] = h->var[1];
+  if (candidate_ms)
+    for (int w = 0; w < 2; ++w)
+      for (int v = 0; v < 3; ++v) candidate_ms[w * 3 + v] = h->tune_ms[w][v];
+  return RVE_OK;
+}
+
+int rve_set_schedule(rve_t h, const int* variants) {
+  if (!h || !variants) return RVE_ERR_ARG;
+  for (int w = 0; w < 2; ++w)
+    if (variants[w] < -1 || variants[w] > 2) return RVE_ERR_ARG;
+  h->var[0] = variants[0];
+  h->var[1] = variants[1];
+  return RVE_OK;
+}
+
 int rve_timing_enable(rve_t h, int enable) {
   if (!h) return RVE_ERR_ARG;
   CK(cudaStreamSynchronize(h->stream));
@@ -1079,6 +1177,10 @@ int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol,
     h->solved = false;
     int rc = ensure_capacity(h, Lg);
     if (rc) { codes[gi] = rc; return; }
+    if (h->var[0] < 0 || h->var[1] < 0) {
+      rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
+      if (rc) { codes[gi] = rc; return; }
+    }
     infos[gi].resize(Lg);
     const int st = (h->precision == RVE_MIXED)
                        ? solve_impl<float>(h, em.data(), Lg, rel_tol, max_iter, infos[gi].data(), h->u, h->emac_d)

@@ -158,3 +158,29 @@ def test_gauss1024_golden(prec):
         C = r.effective_tangent()
     assert code == 0, info
     assert rel_max(C, np.array(ref["C_eff"])) < 1e-9
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_every_tile_variant_gives_the_same_solution(dim):
+    """The autotuner may pick any tile variant of passes A and E: all must agree."""
+    from paper_2105_03297_gb300 import RVE
+    n = (64, 64) if dim == 2 else (64, 32, 16)
+    E = lognormal(n, 61)
+    ns = 3 if dim == 2 else 6
+    Cs = []
+    for va in range(3):
+        for ve in range(3):
+            with RVE(n, precision="mixed") as r:
+                r.set_schedule(va, ve)
+                r.set_material(E, 0.3)
+                code, info = r.solve(np.eye(ns), rel_tol=1e-11, max_iter=3000)
+                assert code == 0, info
+                Cs.append(r.effective_tangent())
+                assert r.schedule()[0] == [va, ve]
+    for C in Cs[1:]:
+        assert rel_max(C, Cs[0]) < 1e-10
+    with RVE(n, precision="mixed") as r:
+        r.set_material(E, 0.3)
+        r.solve(np.eye(ns), rel_tol=1e-11, max_iter=3000)
+        var, ms = r.schedule()
+        assert all(v in (0, 1, 2) for v in var)
