@@ -57,22 +57,31 @@ __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int
                                          bool nodal, T beta, T alpha_prev, bool use_old) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
-  constexpr int NU = NP * (NX / VL);
+  constexpr int D = (GS == 3) ? 2 : 3;
+  // In 3D a unit covers either the three normal or the three shear components
+  // of an element (the material couples only the normal ones through the
+  // trace), which halves the registers a unit needs.
+  constexpr int HALVES = (GS == 6) ? 2 : 1;
+  constexpr int GH = GS / HALVES;
+  constexpr int NU = HALVES * NP * (NX / VL);
   static_assert(LD % 2 == 0, "row starts must stay 16-byte aligned");
   static_assert(VL % 2 == 0, "units pair complex values");
   const int64_t N = a.N;
   T acc = 0;
   for (int i = threadIdx.x; i < NU; i += NT) {
-    const int pr = i / (NX / VL), x0 = (i % (NX / VL)) * VL;
+    const int half = i / (NP * (NX / VL));
+    const int iu = i % (NP * (NX / VL));
+    const int pr = iu / (NX / VL), x0 = (iu % (NX / VL)) * VL;
+    const int j0 = half * GH;
     const int64_t va = v0 + (int64_t)(2 * pr) * NX + x0;
-    T pv[2][GS][VL];
+    T pv[2][GH][VL];
     T ev[2][VL];
     if (nodal) {
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int j = 0; j < GS; ++j) {
-          if (j < a.dim) vloadn<T, VL>(pv[h][j], a.in + ((int64_t)l * a.dim + j) * N + va + h * NX);
+        for (int j = 0; j < GH; ++j) {
+          if (j0 + j < a.dim) vloadn<T, VL>(pv[h][j], a.in + ((int64_t)l * a.dim + j0 + j) * N + va + h * NX);
           else {
 #pragma unroll
             for (int q = 0; q < VL; ++q) pv[h][j][q] = 0;
@@ -83,13 +92,13 @@ __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int
       for (int h = 0; h < 2; ++h) {
         if (a.amode != A_BARE) vloadn<T, VL>(ev[h], a.E + (int64_t)(l / a.lcs) * N + va + h * NX);
 #pragma unroll
-        for (int j = 0; j < GS; ++j) {
-          const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + va + h * NX;
+        for (int j = 0; j < GH; ++j) {
+          const int64_t idx = ((int64_t)l * a.m + c0 + j0 + j) * N + va + h * NX;
           if (a.amode == A_CG) {
             vloadn<T, VL>(pv[h][j], a.r + idx);
           } else if (a.amode == A_MACRO) {
 #pragma unroll
-            for (int q = 0; q < VL; ++q) pv[h][j][q] = (T)a.emac[l * GS + j];
+            for (int q = 0; q < VL; ++q) pv[h][j][q] = (T)a.emac[l * GS + j0 + j];
           } else {
             vloadn<T, VL>(pv[h][j], a.in + idx);
           }
@@ -98,63 +107,67 @@ __device__ __forceinline__ T pass_a_load(const PassArgs<T>& a, cplx<T>* buf, int
       if (a.amode == A_CG && use_old) {
         // deferred update of the previous iteration: x += alpha_prev p_old,
         // then the new direction p = r + beta p_old
-        T po[2][GS][VL], xo[2][GS][VL];
+        T po[2][GH][VL], xo[2][GH][VL];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j) {
-            const int64_t idx = ((int64_t)l * a.m + c0 + j) * N + va + h * NX;
+          for (int j = 0; j < GH; ++j) {
+            const int64_t idx = ((int64_t)l * a.m + c0 + j0 + j) * N + va + h * NX;
             vloadn<T, VL>(po[h][j], a.p + idx);
             vloadn<T, VL>(xo[h][j], a.x + idx);
           }
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j) {
+          for (int j = 0; j < GH; ++j) {
 #pragma unroll
             for (int q = 0; q < VL; ++q) {
               pv[h][j][q] += beta * po[h][j][q];
               xo[h][j][q] += alpha_prev * po[h][j][q];
             }
-            vstoren<T, VL>(a.x + ((int64_t)l * a.m + c0 + j) * N + va + h * NX, xo[h][j]);
+            vstoren<T, VL>(a.x + ((int64_t)l * a.m + c0 + j0 + j) * N + va + h * NX, xo[h][j]);
           }
       }
       if (a.amode == A_CG) {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < GS; ++j) vstoren<T, VL>(a.p + ((int64_t)l * a.m + c0 + j) * N + va + h * NX, pv[h][j]);
+          for (int j = 0; j < GH; ++j)
+            vstoren<T, VL>(a.p + ((int64_t)l * a.m + c0 + j0 + j) * N + va + h * NX, pv[h][j]);
       }
     }
-    T sv[2][GS][VL];
+    T sv[2][GH][VL];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int q = 0; q < VL; ++q) {
         if (nodal || a.amode == A_BARE) {
 #pragma unroll
-          for (int j = 0; j < GS; ++j) sv[h][j][q] = pv[h][j][q];
+          for (int j = 0; j < GH; ++j) sv[h][j][q] = pv[h][j][q];
         } else {
-          // isotropic material, unit-modulus Lame constants times E_v
-          constexpr int D = (GS == 3) ? 2 : 3;
-          T tr = 0;
-#pragma unroll
-          for (int j = 0; j < D; ++j) tr += pv[h][j][q];
-          tr *= a.lam;
+          // isotropic material, unit-modulus Lame constants times E_v:
+          // normal components lambda tr + 2 mu eps, shear components 2 mu eps
           const T e = ev[h][q];
+          if (HALVES == 1 || half == 0) {
+            T tr = 0;
 #pragma unroll
-          for (int j = 0; j < D; ++j) sv[h][j][q] = e * (tr + a.mu2 * pv[h][j][q]);
+            for (int j = 0; j < D; ++j) tr += pv[h][j][q];
+            tr *= a.lam;
 #pragma unroll
-          for (int j = D; j < GS; ++j) sv[h][j][q] = e * (a.mu2 * pv[h][j][q]);
+            for (int j = 0; j < GH; ++j) sv[h][j][q] = (j < D) ? e * (tr + a.mu2 * pv[h][j][q]) : e * (a.mu2 * pv[h][j][q]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < GH; ++j) sv[h][j][q] = e * (a.mu2 * pv[h][j][q]);
+          }
           if (a.amode == A_CG) {
 #pragma unroll
-            for (int j = 0; j < GS; ++j) acc += pv[h][j][q] * sv[h][j][q];
+            for (int j = 0; j < GH; ++j) acc += pv[h][j][q] * sv[h][j][q];
           }
         }
       }
 #pragma unroll
-    for (int j = 0; j < GS; ++j) {
-      C* dst = buf + (j * NP + pr) * LD + x0;
+    for (int j = 0; j < GH; ++j) {
+      C* dst = buf + ((j0 + j) * NP + pr) * LD + x0;
 #pragma unroll
       for (int q = 0; q < VL; q += 2)
         cstore2<T>(dst + q, mkc<T>(sv[0][j][q], sv[1][j][q]), mkc<T>(sv[0][j][q + 1], sv[1][j][q + 1]));
@@ -371,8 +384,8 @@ struct PassEStore {
     const int64_t off = (int64_t)j * a->N + v0 + (int64_t)(2 * pr) * NX + k2;
     const int em = a->emode;
     if (em == E_CG) {
-      // chunks of up to 16 outputs: 32 loads in flight, bounded registers
-      constexpr int CH = N1 < 16 ? N1 : 16;
+      // chunks of up to 8 outputs: 16 loads in flight, bounded registers
+      constexpr int CH = N1 < 8 ? N1 : 8;
       T* r = a->r + idx0 + off;
       T s = 0;
 #pragma unroll

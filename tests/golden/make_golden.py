@@ -8,7 +8,9 @@ oracle's projected CG (O1) on the full grid to a relative residual of
 iteration counts.  ``disc32`` is also solved by the assembled FEM (O2) and
 both results are stored.  ``lognormal64`` additionally stores the oracle's
 adjoint gradient of J = C_1111 at 16 seeded voxels and its Euler sum.
-Nothing here calls the CUDA path.
+``spheres128`` is solved one load case per process (``spheres128:<l>``, each
+writes ``spheres128_lc<l>.json``); ``spheres128:merge`` assembles
+``spheres128.json`` from the six parts.  Nothing here calls the CUDA path.
 """
 import json
 import multiprocessing as mp
@@ -29,6 +31,31 @@ def _run(name):
 
     import microstructures as ms
     from oracle.fe_projection import Problem
+
+    if name.startswith("spheres128:"):
+        part = name.split(":", 1)[1]
+        if part == "merge":
+            parts = [json.load(open(os.path.join(HERE, f"spheres128_lc{l}.json"))) for l in range(6)]
+            S = np.array([p["mean_stress"] for p in parts])     # S[l][:] for unit strain e_l
+            out = dict(name="spheres128", n=parts[0]["n"], nu=parts[0]["nu"], tol=TOL,
+                       source=parts[0]["source"], C_eff=S.T.tolist(),
+                       iterations=[p["iterations"] for p in parts],
+                       seconds=sum(p["seconds"] for p in parts))
+            with open(os.path.join(HERE, "spheres128.json"), "w") as f:
+                json.dump(out, f, indent=1)
+            return name
+        l = int(part)
+        cfg = ms.config_inputs("spheres128")
+        t0 = time.time()
+        P = Problem(cfg["n"], cfg["E"], cfg["nu"])
+        eps, it, res = P.solve(np.eye(6)[l], tol=TOL)
+        out = dict(name=f"spheres128 load case {l}", n=list(cfg["n"]), nu=cfg["nu"], tol=TOL,
+                   source="oracle.fe_projection.Problem (O1), FP64, numpy FFT",
+                   mean_stress=P.mean_stress(eps).tolist(), iterations=it, rel_residual=float(res),
+                   seconds=time.time() - t0)
+        with open(os.path.join(HERE, f"spheres128_lc{l}.json"), "w") as f:
+            json.dump(out, f, indent=1)
+        return name
 
     cfg = ms.config_inputs(name)
     t0 = time.time()
