@@ -189,6 +189,115 @@ __device__ __forceinline__ void project_3d(cplx<T>* col, const cplx<T>* e, const
   }
 }
 
+// The same projection done by a pair of adjacent lanes: lane half h handles
+// tetrahedra 3h..3h+2 (their gradients, their share of B^H B and of
+// t = B^H s), the pair exchanges its partial sums by warp shuffle, both
+// solve the 3x3 system, and each writes the outputs of its own tetrahedra.
+// All 32 lanes of a warp must call it together (it exchanges partial sums
+// with __shfl_xor_sync over the full warp): the k = 0 wavevector is handled by
+// the `zero` flag, which only changes what is written at the end.
+template <typename T, int LD>
+__device__ __forceinline__ void project_3d_pair(cplx<T>* col, const cplx<T>* e, const T* ih, T scale, int mode,
+                                                int half, bool zero) {
+  using C = cplx<T>;
+  const C one = mkc<T>(1, 0);
+  C d[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d[i] = cscale(csub(e[i], one), ih[i]);
+  const C e01 = cmul(e[0], e[1]), e02 = cmul(e[0], e[2]), e12 = cmul(e[1], e[2]);
+  // gradients of this lane's tetrahedra {0, e_a, e_a+e_b, 1}
+  C g[3][3];
+  if (half == 0) {
+    g[0][0] = d[0];             g[0][1] = cmul(e[0], d[1]);  g[0][2] = cmul(e01, d[2]);   // (x,y,z)
+    g[1][0] = d[0];             g[1][1] = cmul(e02, d[1]);   g[1][2] = cmul(e[0], d[2]);  // (x,z,y)
+    g[2][0] = cmul(e[1], d[0]); g[2][1] = d[1];              g[2][2] = cmul(e01, d[2]);   // (y,x,z)
+  } else {
+    g[0][0] = cmul(e12, d[0]);  g[0][1] = d[1];              g[0][2] = cmul(e[1], d[2]);  // (y,z,x)
+    g[1][0] = cmul(e[2], d[0]); g[1][1] = cmul(e02, d[1]);   g[1][2] = d[2];              // (z,x,y)
+    g[2][0] = cmul(e12, d[0]);  g[2][1] = cmul(e[2], d[1]);  g[2][2] = d[2];              // (z,y,x)
+  }
+  // partial M = B^H B over this lane's tetrahedra
+  T md[3] = {0, 0, 0};
+  C m01 = mkc<T>(0, 0), m02 = mkc<T>(0, 0), m12 = mkc<T>(0, 0);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const T a0 = cabs2(g[t][0]), a1 = cabs2(g[t][1]), a2 = cabs2(g[t][2]);
+    const T nn = a0 + a1 + a2;
+    md[0] += (T)0.5 * (nn + a0);
+    md[1] += (T)0.5 * (nn + a1);
+    md[2] += (T)0.5 * (nn + a2);
+    m01 = cadd(m01, cscale(cmul(g[t][0], cconj(g[t][1])), (T)0.5));
+    m02 = cadd(m02, cscale(cmul(g[t][0], cconj(g[t][2])), (T)0.5));
+    m12 = cadd(m12, cscale(cmul(g[t][1], cconj(g[t][2])), (T)0.5));
+  }
+  const T r2 = (T)kInvSqrt2;
+  C t3[3];
+  cplx<T>* own = col + 18 * half * LD;  // rows of this lane's tetrahedra
+  if (mode == P_NODAL_IN) {
+    t3[0] = col[0]; t3[1] = col[LD]; t3[2] = col[2 * LD];
+  } else {
+    t3[0] = t3[1] = t3[2] = mkc<T>(0, 0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const C* sp = own + 6 * t * LD;
+      const C sxx = sp[0], syy = sp[LD], szz = sp[2 * LD];
+      const C syz = cscale(sp[3 * LD], r2), sxz = cscale(sp[4 * LD], r2), sxy = cscale(sp[5 * LD], r2);
+      t3[0] = cadd(t3[0], cadd(cadd(cjmul(g[t][0], sxx), cjmul(g[t][1], sxy)), cjmul(g[t][2], sxz)));
+      t3[1] = cadd(t3[1], cadd(cadd(cjmul(g[t][0], sxy), cjmul(g[t][1], syy)), cjmul(g[t][2], syz)));
+      t3[2] = cadd(t3[2], cadd(cadd(cjmul(g[t][0], sxz), cjmul(g[t][1], syz)), cjmul(g[t][2], szz)));
+    }
+  }
+  // pair sums
+  auto xs = [](T v) { return v + __shfl_xor_sync(0xffffffffu, v, 1); };
+#pragma unroll
+  for (int i = 0; i < 3; ++i) md[i] = xs(md[i]);
+  m01.x = xs(m01.x); m01.y = xs(m01.y);
+  m02.x = xs(m02.x); m02.y = xs(m02.y);
+  m12.x = xs(m12.x); m12.y = xs(m12.y);
+  if (mode != P_NODAL_IN) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { t3[i].x = xs(t3[i].x); t3[i].y = xs(t3[i].y); }
+  }
+  const T A = md[0], B = md[1], Cc = md[2];
+  const T A00 = B * Cc - cabs2(m12);
+  const T A11 = A * Cc - cabs2(m02);
+  const T A22 = A * B - cabs2(m01);
+  const C A01 = csub(cmul(m02, cconj(m12)), cscale(m01, Cc));
+  const C A02 = csub(cmul(m01, m12), cscale(m02, B));
+  const C A12 = csub(cmul(m02, cconj(m01)), cscale(m12, A));
+  const T det = A * A00 + (cmul(m01, cconj(A01))).x + (cmul(m02, cconj(A02))).x;
+  const T id = scale / det;
+  C w[3];
+  w[0] = cscale(cadd(cadd(cscale(t3[0], A00), cmul(A01, t3[1])), cmul(A02, t3[2])), id);
+  w[1] = cscale(cadd(cadd(cjmul(A01, t3[0]), cscale(t3[1], A11)), cmul(A12, t3[2])), id);
+  w[2] = cscale(cadd(cadd(cjmul(A02, t3[0]), cjmul(A12, t3[1])), cscale(t3[2], A22)), id);
+  if (zero) {
+    // k = 0: G(0) = 0, the fluctuation has no mean (w is not finite here)
+    const C z = mkc<T>(0, 0);
+    if (mode == P_NODAL_OUT) {
+      if (half == 0) { col[0] = z; col[LD] = z; col[2 * LD] = z; }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 18; ++r) own[r * LD] = z;
+    }
+    return;
+  }
+  if (mode == P_NODAL_OUT) {
+    if (half == 0) { col[0] = w[0]; col[LD] = w[1]; col[2 * LD] = w[2]; }
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    C* sp = own + 6 * t * LD;
+    sp[0] = cmul(g[t][0], w[0]);
+    sp[LD] = cmul(g[t][1], w[1]);
+    sp[2 * LD] = cmul(g[t][2], w[2]);
+    sp[3 * LD] = cscale(cadd(cmul(g[t][1], w[2]), cmul(g[t][2], w[1])), r2);
+    sp[4 * LD] = cscale(cadd(cmul(g[t][0], w[2]), cmul(g[t][2], w[0])), r2);
+    sp[5 * LD] = cscale(cadd(cmul(g[t][0], w[1]), cmul(g[t][1], w[0])), r2);
+  }
+}
+
 // grid (n_x/2+1, n_y, L): one (k_x, k_y) pencil of all components per block.
 template <typename T, int NZ, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs<T> a) {
@@ -213,13 +322,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
   C e[3];
   e[0] = a.ph[0][kx];
   e[1] = a.ph[1][ky];
-  for (int kz = threadIdx.x; kz < NZ; kz += NT) {
-    if (kx == 0 && ky == 0 && kz == 0) {
-      for (int c = 0; c < cout; ++c) buf[c * LD] = mkc<T>(0, 0);
-    } else {
-      e[2] = a.ph[2][kz];
-      project_3d<T, LD>(buf + kz, e, a.ih, a.inv_n, a.pmode);
-    }
+  // two lanes per wavevector (NT >= 2 NZ, and 2 NZ is a whole number of warps)
+  static_assert(NT >= 2 * NZ && (2 * NZ) % 32 == 0, "pass C needs two lanes per wavevector");
+  if (threadIdx.x < 2 * NZ) {  // whole warps: every lane of them calls the pair projection
+    const int kz = threadIdx.x >> 1, half = threadIdx.x & 1;
+    e[2] = a.ph[2][kz];
+    project_3d_pair<T, LD>(buf + kz, e, a.ih, a.inv_n, a.pmode, half, kx == 0 && ky == 0 && kz == 0);
   }
   __syncthreads();
   auto ld_s = [&](int c, int z) -> C { return buf[c * LD + z]; };
