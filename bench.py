@@ -356,6 +356,43 @@ def run_gpu(args):
 
     value = world * 1000.0 / ms_step
     launches = int(sum(v[1] for v in kt.values()))
+
+    extras = {}
+    if rank == 0 and not args.no_comparisons:
+        # the plain FP64 GPU solve of the same workload, to the same tolerance
+        if prec == "mixed":
+            with RVE(n, precision="fp64", stream=stream.cuda_stream) as r64:
+                r64.set_material(E_dev, nu)
+                r64.solve(Em, rel_tol=tol, max_iter=max_iter)      # warm-up (and autotune)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                code64, info64 = r64.solve(Em, rel_tol=tol, max_iter=max_iter)
+                C64 = r64.effective_tangent() if L == ns else r64.mean_stress()
+                torch.cuda.synchronize()
+                t64 = time.perf_counter() - t0
+            d64 = float(np.abs(C - C64).max() / np.abs(C64).max())
+            extras["fp64_gpu_solve"] = {"ms_per_solve": t64 * 1e3, "speedup_of_mixed": t64 * 1e3 / ms_step,
+                                        "iterations": [i["iterations"] for i in info64],
+                                        "mixed_vs_fp64_rel_diff": d64}
+        # cuFFT (through torch.fft) on the same fields: context only, not part of the product
+        m = (2 if dim == 2 else 6) * ns
+        shape = (L * m,) + tuple(reversed(n))
+        f = torch.randn(shape, device="cuda", dtype=torch.float32 if prec == "mixed" else torch.float64)
+        dims = tuple(range(1, dim + 1))
+        for _ in range(3):
+            g = torch.fft.irfftn(torch.fft.rfftn(f, dim=dims), s=shape[1:], dim=dims)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            g = torch.fft.irfftn(torch.fft.rfftn(f, dim=dims), s=shape[1:], dim=dims)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ours = sum(v[0] for k, v in kt.items() if k in mb) / (cg_iters * args.steps)
+        extras["cufft_r2c_c2r_same_fields"] = {"ms": e0.elapsed_time(e1) / 5,
+                                               "our_full_cg_iteration_ms": ours,
+                                               "note": "cuFFT forward+inverse only (no material, projection "
+                                                       "or CG update); context, not used by the solver"}
+        del f, g
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -376,6 +413,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    out.update(extras)
     if rank == 0 and not args.no_cpu_baseline:
         its_gold, _ = golden_iterations(cfg_name)
         total_its = sum(its_gold) if its_gold else lc_iters
@@ -399,6 +437,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="gauss1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the FP64 GPU solve and cuFFT timings (context figures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
