@@ -39,6 +39,21 @@ WORKLOADS = {
 }
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest value over all ranks (the slowest rank sets the job time)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world):
+    """Whole-job rate: every rank processes its own units (replicas, weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -229,10 +244,7 @@ def run_batch(args, world, rank, local, dist):
             iters.append(max(v["iterations"] for rv in info for v in rv))
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dt, dist if world > 1 else None, "cuda")
     # model bytes of every slot's CG iterations in this step (7 vector + 4 spectrum streams, FP32)
     total_bytes = 0.0
     for (n, _), rv in zip(rves, info):
@@ -241,7 +253,7 @@ def run_batch(args, world, rank, local, dist):
     peak, peak_kind = peaks()
     achieved = total_bytes / dt / 1e9
     out = {
-        "metric": METRIC, "value": world * len(sizes) / dt, "unit": "RVE solves/s (3 load cases each)",
+        "metric": METRIC, "value": job_throughput(len(sizes), dt, world), "unit": "RVE solves/s (3 load cases each)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": cfg_name, "rves": len(sizes), "voxels": int(sum(np.prod(n) for n in sizes)),
@@ -317,11 +329,8 @@ def run_gpu(args):
             iters.append([i["iterations"] for i in info])
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist if world > 1 else None, "cuda")
     if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     kt = r.timing_read()
     r.timing(False)
@@ -348,13 +357,9 @@ def run_gpu(args):
         r.solve(Em, rel_tol=tol, max_iter=max_iter)
         C_h = homogenised()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist if world > 1 else None, "cuda")
 
-    value = world * 1000.0 / ms_step
+    value = job_throughput(1.0, ms_step / 1000.0, world)
     launches = int(sum(v[1] for v in kt.values()))
 
     extras = {}
@@ -408,7 +413,7 @@ def run_gpu(args):
                      "peak_source": peak_kind},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant"), r.schedule()[0])),
-        "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(E_host.nbytes + Em.nbytes),
+        "e2e": {"value": job_throughput(1.0, e2e_s, world), "unit": "solves/s", "h2d_bytes_per_step": int(E_host.nbytes + Em.nbytes),
                 "d2h_bytes_per_step": int(C_h.nbytes)},
         "gpu_launches": launches,
         "clocks": clk.summary(),

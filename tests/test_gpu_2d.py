@@ -184,3 +184,18 @@ def test_every_tile_variant_gives_the_same_solution(dim):
         r.solve(np.eye(ns), rel_tol=1e-11, max_iter=3000)
         var, ms = r.schedule()
         assert all(v in (0, 1, 2) for v in var)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_anisotropic_voxels(prec):
+    """Cell lengths enter through the voxel sizes h_a = L_a / n_a (Appendix A)."""
+    from paper_2105_03297_gb300 import RVE
+    n, length = (32, 16), (2.0, 0.5)
+    E = lognormal(n, 71)
+    C_ref, _, _ = Problem(n, E, 0.3, length=length).effective_tangent(np.eye(3), tol=1e-13)
+    with RVE(n, precision=prec, length=length) as r:
+        r.set_material(E, 0.3)
+        code, info = r.solve(np.eye(3), rel_tol=1e-12, max_iter=3000)
+        C = r.effective_tangent()
+    assert code == 0, info
+    assert rel_max(C, C_ref) < 1e-9

@@ -114,3 +114,16 @@ def test_lognormal64_golden(prec):
     gs = g[np.array(ref["adjoint_voxels"])]
     assert rel_max(gs, np.array(ref["adjoint_grad"])) < 1e-9
     assert abs(np.sum(cfg["E"].reshape(-1) * g) - ref["adjoint_euler_sum"]) < 1e-9 * abs(ref["adjoint_euler_sum"])
+
+
+def test_anisotropic_voxels_3d():
+    from paper_2105_03297_gb300 import RVE
+    n, length = (16, 32, 16), (1.0, 3.0, 0.25)
+    E = lognormal(n, 72)
+    C_ref, _, _ = Problem(n, E, 0.3, length=length).effective_tangent(np.eye(6), tol=1e-13)
+    with RVE(n, precision="mixed", length=length) as r:
+        r.set_material(E, 0.3)
+        code, info = r.solve(np.eye(6), rel_tol=1e-12, max_iter=3000)
+        C = r.effective_tangent()
+    assert code == 0, info
+    assert rel_max(C, C_ref) < 1e-9
