@@ -63,19 +63,36 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def model_bytes(dim, n, s, L_iters):
+def model_bytes(dim, n, s, L_iters, form="stress"):
     """Algorithmic bytes of the CG-iteration passes, per load-case iteration.
 
     s: bytes per real scalar of the inner precision.  Returns dict pass -> bytes.
-    Pass A reads r, p_old, x and E and writes p, x (the deferred x += alpha p)
-    and the x-spectrum; pass C (2D) reads and writes the spectrum once; pass E
-    reads the spectrum and r and writes r.  In 3D passes B, C, D each read and
-    write the spectrum.
+    Stress form: pass A reads r, p_old, x and E and writes p, x (the deferred
+    x += alpha p) and the x-spectrum; pass C (2D) reads and writes the spectrum
+    once; pass E reads the spectrum and r and writes r.  In 3D passes B, C, D
+    each read and write the spectrum.
+    Factored form: the force stencil reads r, p_old, x, E and writes p, x and
+    the D nodal forces; the FFT passes move D-component spectra (pass A reads
+    the forces, pass E writes w); the strain update reads w and r, writes r.
     """
     nq, ns = (2, 3) if dim == 2 else (6, 6)
     m = nq * ns
     N = int(np.prod(n))
     kx = n[0] // 2 + 1
+    if form == "factored":
+        D = dim
+        specd = D * kx * (N // n[0]) * 2 * s
+        out = {
+            "force_stencil": (5 * m + 1 + D) * N * s,
+            "pass_a": D * N * s + specd,
+            "pass_c": 2 * specd,
+            "pass_e": specd + D * N * s,
+            "strain_update": (D + 2 * m) * N * s,
+        }
+        if dim == 3:
+            out["pass_b"] = 2 * specd
+            out["pass_d"] = 2 * specd
+        return out
     spec = m * kx * (N // n[0]) * 2 * s
     out = {
         "pass_a": 5 * m * N * s + N * s + spec,
@@ -299,6 +316,9 @@ def run_gpu(args):
     L = len(Em)
     stream = torch.cuda.current_stream()
     r = RVE(n, precision=prec, stream=stream.cuda_stream)
+    if args.schedule:
+        r.set_schedule(*[int(v) for v in args.schedule.split(",")])
+    r.set_operator_form(args.form)
     E_dev = torch.from_numpy(E.reshape(-1)).cuda()
     r.set_material(E_dev, nu)
     max_iter = 20000
@@ -338,7 +358,7 @@ def run_gpu(args):
     lc_iters = float(np.sum(iters)) / args.steps          # load-case iterations per solve
     cg_iters = float(np.mean([max(v) for v in iters]))   # batched iterations per solve
     s = 4 if prec == "mixed" else 8
-    mb = model_bytes(dim, n, s, lc_iters)
+    mb = model_bytes(dim, n, s, lc_iters, args.form)
     # dominant kernel: the CG-iteration pass with the most device time
     cand = {k: v for k, v in kt.items() if k in mb and v[1] > 0}
     dom = max(cand, key=lambda k: cand[k][0])
@@ -379,6 +399,25 @@ def run_gpu(args):
             extras["fp64_gpu_solve"] = {"ms_per_solve": t64 * 1e3, "speedup_of_mixed": t64 * 1e3 / ms_step,
                                         "iterations": [i["iterations"] for i in info64],
                                         "mixed_vs_fp64_rel_diff": d64}
+        # the other order of the same operator, same workload and tolerance
+        other = "factored" if args.form == "stress" else "stress"
+        with RVE(n, precision=prec, stream=stream.cuda_stream) as ro:
+            ro.set_operator_form(other)
+            ro.set_material(E_dev, nu)
+            ro.solve(Em, rel_tol=tol, max_iter=max_iter)          # warm-up (and autotune)
+            torch.cuda.synchronize()
+            eo0, eo1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            eo0.record(stream)
+            codeo, infoo = ro.solve(Em, rel_tol=tol, max_iter=max_iter)
+            Co = ro.effective_tangent() if L == ns else ro.mean_stress()
+            eo1.record(stream)
+            torch.cuda.synchronize()
+            t_o = eo0.elapsed_time(eo1)
+        its_o = [i["iterations"] for i in infoo]
+        extras[f"{other}_form_solve"] = {
+            "ms_per_solve": t_o, "ratio_to_headline": t_o / ms_step, "iterations": its_o,
+            "ms_per_cg_iteration": t_o / max(its_o),
+            "rel_diff_to_headline": float(np.abs(C - Co).max() / np.abs(Co).max())}
         # cuFFT (through torch.fft) on the same fields: context only, not part of the product
         m = (2 if dim == 2 else 6) * ns
         shape = (L * m,) + tuple(reversed(n))
@@ -403,7 +442,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": cfg_name, "grid": list(n), "load_cases": L, "precision": prec,
-                   "rel_tol": tol, "parallelism": f"replicas{world}",
+                   "rel_tol": tol, "operator_form": args.form, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (working set > 129 MB)"},
         "ms_per_cg_iteration": cg_ms,
         "cg_iterations_per_solve": cg_iters,
@@ -442,6 +481,10 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="gauss1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="",
+                    help="force the tile variants of passes A and E, e.g. 0,0 (default: autotune)")
+    ap.add_argument("--form", default="stress", choices=["stress", "factored"],
+                    help="order of the operator inside CG (same operator; see include/rve.h)")
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the FP64 GPU solve and cuFFT timings (context figures)")
     args = ap.parse_args()

@@ -161,16 +161,41 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
 int rve_schedule(rve_t h, int* variants, float* candidate_ms);
 int rve_set_schedule(rve_t h, const int* variants);
 
+/* Order of the projected operator inside the CG iterations.  Both forms apply
+ * the same operator G C (Eq. stat-mech-equi-FFT-homogenization with the
+ * projection of Eqs. discrete_projection_op and small-strain-eq2), so the CG
+ * iterates agree up to rounding:
+ *   RVE_FORM_STRESS   (default) forward FFT of every stress component, the
+ *                     projection B (B^H B)^-1 B^H at each wavevector, inverse
+ *                     FFT of every strain component.
+ *   RVE_FORM_FACTORED the same chain split where Appendix B splits it: the
+ *                     right-hand side of Eq. small-strain-eq2 (B^H applied to
+ *                     the stresses) is formed in real space as nodal forces
+ *                     with the element stencils of Eq. discrderiv, only the D
+ *                     nodal components are FFT'd and multiplied by the
+ *                     inverse normal matrix (B^H B)^-1 (Eq. small-strain-chi),
+ *                     and the strains of Eq. small-strain are formed back in
+ *                     real space with the same stencils.  It needs one more
+ *                     direction field [L][m][N] of the inner precision.
+ * rve_set_operator_form applies from the next solve; returns RVE_ERR_ARG for
+ * an unknown form, RVE_ERR_OOM if the extra field cannot be allocated. */
+#define RVE_FORM_STRESS 0
+#define RVE_FORM_FACTORED 1
+int rve_set_operator_form(rve_t h, int form);
+int rve_operator_form(rve_t h, int* form);
+
 /* Measurement hooks (not part of the method).  With timing enabled, every
  * kernel launch of the solver is bracketed by CUDA events on the handle's
  * stream; rve_timing_read returns, per kernel kind, the summed device time in
  * milliseconds and the number of launches since the last read, and resets
  * them.  Kinds (index), counting launches inside projected-CG iterations:
- * 0 pass A (material + x FFT), 1 pass B (y FFT, 3D), 2 pass C (last-axis FFT
- * + projection), 3 pass D (inverse y FFT, 3D), 4 pass E (inverse x FFT + CG
- * update); 5 the FP64 residual; 6 every other launch (right-hand side,
- * displacement recovery, homogenisation). */
-#define RVE_NKINDS 7
+ * 0 pass A (material + x FFT; factored form: x FFT of the nodal forces),
+ * 1 pass B (y FFT, 3D), 2 pass C (last-axis FFT + projection or nodal solve),
+ * 3 pass D (inverse y FFT, 3D), 4 pass E (inverse x FFT + CG update; factored
+ * form: inverse x FFT of w); 5 the FP64 residual; 6 every other launch
+ * (right-hand side, displacement recovery, homogenisation); 7 the force
+ * stencil and 8 the strain update of the factored form. */
+#define RVE_NKINDS 9
 int rve_timing_enable(rve_t h, int enable);
 int rve_timing_read(rve_t h, double* ms /*[RVE_NKINDS]*/, int64_t* launches /*[RVE_NKINDS]*/);
 

@@ -53,6 +53,8 @@ SIGNATURES = {
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "rve_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "rve_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "rve_set_operator_form": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_operator_form": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "rve_timing_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "rve_apply_operator_2d_static": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_void_p,
@@ -221,14 +223,27 @@ class RVE:
         v = (C.c_int * 2)(int(var_a), int(var_e))
         _check(load().rve_set_schedule(self.h, v), "rve_set_schedule")
 
-    KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other")
+    FORMS = {"stress": 0, "factored": 1}
+
+    def set_operator_form(self, form):
+        """'stress' (default: FFT of every stress component) or 'factored'
+        (real-space nodal forces, FFT of the D nodal components only)."""
+        _check(load().rve_set_operator_form(self.h, self.FORMS[form]), "rve_set_operator_form")
+
+    def operator_form(self):
+        f = C.c_int()
+        _check(load().rve_operator_form(self.h, C.byref(f)), "rve_operator_form")
+        return {v: k for k, v in self.FORMS.items()}[f.value]
+
+    KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other", "force_stencil",
+             "strain_update")
 
     def timing(self, enable):
         _check(load().rve_timing_enable(self.h, 1 if enable else 0), "rve_timing_enable")
 
     def timing_read(self):
-        ms = (C.c_double * 7)()
-        cnt = (C.c_int64 * 7)()
+        ms = (C.c_double * len(self.KINDS))()
+        cnt = (C.c_int64 * len(self.KINDS))()
         _check(load().rve_timing_read(self.h, ms, cnt), "rve_timing_read")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KINDS)}
 

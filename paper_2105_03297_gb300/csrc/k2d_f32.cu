@@ -1,8 +1,10 @@
 // 2D pass kernels, FP32 instances (inner solve of the mixed-precision path).
-#include "pass2d.cuh"
+#include "factored.cuh"
 namespace rve {
 template cudaError_t launch_pass_a_2d<float>(const PassArgs<float>&, cudaStream_t);
 template cudaError_t launch_pass_c_2d<float>(const PassArgs<float>&, cudaStream_t);
 template cudaError_t launch_pass_e_2d<float>(const PassArgs<float>&, cudaStream_t);
 template cudaError_t launch_cg_finish_x<float>(const PassArgs<float>&, cudaStream_t);
+template cudaError_t launch_force_stencil<float>(const PassArgs<float>&, const float*, float*, float*, cudaStream_t);
+template cudaError_t launch_strain_update<float>(const PassArgs<float>&, const float*, cudaStream_t);
 }  // namespace rve

@@ -264,7 +264,7 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
     m01 = cadd(m01, cscale(cmul(g[q][0], cconj(g[q][1])), (T)0.5));
   }
   C t0, t1;
-  if (mode == P_NODAL_IN) {
+  if (mode == P_NODAL_IN || mode == P_SOLVE) {
     t0 = s[0]; t1 = s[1];
   } else {
     // t = B^H s: t_j = sum_q sum_a conj(g_qa) sigma_q,aj
@@ -281,7 +281,7 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
   // w = M^-1 t,  M^-1 = [[m11, -m01], [-conj(m01), m00]] / det
   const C w0 = cscale(csub(cscale(t0, m11), cmul(m01, t1)), id);
   const C w1 = cscale(csub(cscale(t1, m00), cjmul(m01, t0)), id);
-  if (mode == P_NODAL_OUT) {
+  if (mode == P_NODAL_OUT || mode == P_SOLVE) {
     s[0] = w0; s[1] = w1;
     return;
   }
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
-  const int cin = (a.pmode == P_NODAL_IN) ? 2 : M;
-  const int cout = (a.pmode == P_NODAL_OUT) ? 2 : M;
+  const int cin = (a.pmode == P_NODAL_IN || a.pmode == P_SOLVE) ? 2 : M;
+  const int cout = (a.pmode == P_NODAL_OUT || a.pmode == P_SOLVE) ? 2 : M;
   C* col = a.spec + (((int64_t)l * M) * KX + kx) * NY;
   const int64_t cstride = (int64_t)KX * NY;
   auto ld_g = [&](int c, int y) -> C { return col[c * cstride + y]; };
@@ -416,6 +416,10 @@ struct PassEStore {
         s += q[k1].x * q[k1].x + q[k1].y * q[k1].y;
       }
       *acc += s;
+    } else if (em == E_NOUT) {
+      T* o = a->out + uidx0 + off;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) { o[N2 * k1] = q[k1].x; o[NX + N2 * k1] = q[k1].y; }
     } else if (em == E_OUT) {
       T* o = a->out + idx0 + off;
 #pragma unroll
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pas
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
-  const bool nodal = (a.emode == E_NODAL);
+  const bool nodal = (a.emode == E_NODAL || a.emode == E_NOUT);
   const int ge = nodal ? 2 : GE;
   const int c0 = nodal ? 0 : grp * GE;
 
@@ -495,7 +499,9 @@ __global__ void __launch_bounds__(NT) cg_finish_x(PassArgs<T> a) {
   const int64_t idx = (int64_t)l * a.m * a.N + i * VL;
   T xv[VL], pv[VL];
   vload(xv, a.x + idx);
-  vload(pv, a.p + idx);
+  // the factored form alternates the direction between p (even iterations) and p2 (odd)
+  const T* pl = (a.p2 != nullptr && ((cg->it - 1) & 1)) ? a.p2 : a.p;
+  vload(pv, pl + idx);
 #pragma unroll
   for (int w = 0; w < VL; ++w) xv[w] += alpha * pv[w];
   vstore(a.x + idx, xv);
@@ -538,7 +544,7 @@ cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_e_2d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.emode == E_NODAL ? 1 : 2, a.L);
+  dim3 grid(a.n[1] / TY, (a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : 2, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }

@@ -233,7 +233,8 @@ __device__ __forceinline__ void project_3d_pair(cplx<T>* col, const cplx<T>* e, 
   const T r2 = (T)kInvSqrt2;
   C t3[3];
   cplx<T>* own = col + 18 * half * LD;  // rows of this lane's tetrahedra
-  if (mode == P_NODAL_IN) {
+  const bool nodal_in = (mode == P_NODAL_IN || mode == P_SOLVE);
+  if (nodal_in) {
     t3[0] = col[0]; t3[1] = col[LD]; t3[2] = col[2 * LD];
   } else {
     t3[0] = t3[1] = t3[2] = mkc<T>(0, 0);
@@ -254,7 +255,7 @@ __device__ __forceinline__ void project_3d_pair(cplx<T>* col, const cplx<T>* e, 
   m01.x = xs(m01.x); m01.y = xs(m01.y);
   m02.x = xs(m02.x); m02.y = xs(m02.y);
   m12.x = xs(m12.x); m12.y = xs(m12.y);
-  if (mode != P_NODAL_IN) {
+  if (!nodal_in) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) { t3[i].x = xs(t3[i].x); t3[i].y = xs(t3[i].y); }
   }
@@ -271,10 +272,11 @@ __device__ __forceinline__ void project_3d_pair(cplx<T>* col, const cplx<T>* e, 
   w[0] = cscale(cadd(cadd(cscale(t3[0], A00), cmul(A01, t3[1])), cmul(A02, t3[2])), id);
   w[1] = cscale(cadd(cadd(cjmul(A01, t3[0]), cscale(t3[1], A11)), cmul(A12, t3[2])), id);
   w[2] = cscale(cadd(cadd(cjmul(A02, t3[0]), cjmul(A12, t3[1])), cscale(t3[2], A22)), id);
+  const bool nodal_out = (mode == P_NODAL_OUT || mode == P_SOLVE);
   if (zero) {
     // k = 0: G(0) = 0, the fluctuation has no mean (w is not finite here)
     const C z = mkc<T>(0, 0);
-    if (mode == P_NODAL_OUT) {
+    if (nodal_out) {
       if (half == 0) { col[0] = z; col[LD] = z; col[2 * LD] = z; }
     } else {
 #pragma unroll
@@ -282,7 +284,7 @@ __device__ __forceinline__ void project_3d_pair(cplx<T>* col, const cplx<T>* e, 
     }
     return;
   }
-  if (mode == P_NODAL_OUT) {
+  if (nodal_out) {
     if (half == 0) { col[0] = w[0]; col[LD] = w[1]; col[2 * LD] = w[2]; }
     return;
   }
@@ -311,8 +313,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
-  const int cin = (a.pmode == P_NODAL_IN) ? 3 : M;
-  const int cout = (a.pmode == P_NODAL_OUT) ? 3 : M;
+  const int cin = (a.pmode == P_NODAL_IN || a.pmode == P_SOLVE) ? 3 : M;
+  const int cout = (a.pmode == P_NODAL_OUT || a.pmode == P_SOLVE) ? 3 : M;
   const int64_t stride_c = (int64_t)KX * ny * NZ;
   C* pen = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
   auto ld_g = [&](int c, int z) -> C { return pen[c * stride_c + z]; };
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
   C* buf = reinterpret_cast<C*>(smem_raw);  // [GE][NP][LD]
   __shared__ double red[NT / 32];
   __shared__ int flag;
-  const bool nodal = (a.emode == E_NODAL);
+  const bool nodal = (a.emode == E_NODAL || a.emode == E_NOUT);
   const int G = nodal ? 1 : 6;
   const int l = blockIdx.z / G, grp = blockIdx.z % G;
   const int z = blockIdx.y, y0 = blockIdx.x * TY;
@@ -412,7 +414,7 @@ cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_e_3d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.emode == E_NODAL ? 1 : 6));
+  dim3 grid(a.n[1] / TY, a.n[2], a.L * ((a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : 6));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -440,7 +442,9 @@ cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_y_3d<T, NY, TZB, NT, FWD>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  const int Cc = FWD ? (a.pmode == P_NODAL_IN ? 3 : a.m) : (a.pmode == P_NODAL_OUT ? 3 : a.m);
+  const bool din = (a.pmode == P_NODAL_IN || a.pmode == P_SOLVE);
+  const bool dout = (a.pmode == P_NODAL_OUT || a.pmode == P_SOLVE);
+  const int Cc = FWD ? (din ? 3 : a.m) : (dout ? 3 : a.m);
   dim3 grid(a.n[2] / TZB, a.kx, a.L * Cc);
   k<<<grid, NT, sm, s>>>(a, Cc);
   return cudaGetLastError();

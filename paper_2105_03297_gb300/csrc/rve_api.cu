@@ -47,6 +47,7 @@ struct rve_s {
   double* E64 = nullptr;
   void* Ein = nullptr;  // E in the inner precision (aliases E64 for FP64)
   void* x = nullptr; void* r = nullptr; void* p = nullptr;
+  void* p2 = nullptr;   // second direction buffer (factored operator form only)
   void* fbuf = nullptr;
   void* spec = nullptr; void* spec2 = nullptr;
   double* u = nullptr;
@@ -78,6 +79,7 @@ struct rve_s {
   CgState* cg_h2 = nullptr;               // second pinned copy of the CG state (run-ahead)
   int var[2] = {-1, -1};                  // tile variants of passes A and E (-1 = autotune at first solve)
   float tune_ms[2][3] = {{0}};            // measured times of the candidates (last tuning)
+  int op_form = RVE_FORM_STRESS;          // order of the operator inside projected CG
 };
 
 namespace {
@@ -93,7 +95,7 @@ int map_err(cudaError_t e) {
   return RVE_ERR_CUDA;
 }
 
-enum { K_A = 0, K_B = 1, K_C = 2, K_D = 3, K_E = 4, K_RES = 5, K_OTHER = 6 };
+enum { K_A = 0, K_B = 1, K_C = 2, K_D = 3, K_E = 4, K_RES = 5, K_OTHER = 6, K_FS = 7, K_SU = 8 };
 
 // Launch fn() on the handle's stream; with timing on, bracket it with events.
 template <typename F> cudaError_t timed(rve_s* h, int kind, F fn) {
@@ -188,7 +190,7 @@ int64_t spec_elems(const rve_s* h) {
 }
 
 void free_L(rve_s* h) {
-  free_dev(h->x); free_dev(h->r); free_dev(h->p); free_dev(h->fbuf);
+  free_dev(h->x); free_dev(h->r); free_dev(h->p); free_dev(h->p2); free_dev(h->fbuf);
   free_dev(h->spec); free_dev(h->spec2);
   free_devp(h->u); free_devp(h->uadj); free_devp(h->part); free_devp(h->cg);
   free_devp(h->emac_d); free_devp(h->emac_adj_d);
@@ -222,6 +224,8 @@ int ensure_capacity(rve_s* h, int L) {
       (rc = dev_alloc(&h->fbuf, fld)) || (rc = dev_alloc(&h->spec, sp)))
     { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
   if (h->dim == 3 && (rc = dev_alloc(&h->spec2, sp))) { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
+  if (h->op_form == RVE_FORM_FACTORED && (rc = dev_alloc(&h->p2, fld)))
+    { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
   if ((rc = dev_alloc((void**)&h->u, (size_t)L * h->D * h->N * sizeof(double))) ||
       (rc = dev_alloc((void**)&h->uadj, (size_t)h->ns * h->D * h->N * sizeof(double))))
     { free_L(h); if (keep_u) cudaFree(keep_u); return rc; }
@@ -237,6 +241,7 @@ int ensure_capacity(rve_s* h, int L) {
     cudaGetLastError(); free_L(h); if (keep_u) cudaFree(keep_u); return RVE_ERR_OOM;
   }
   cudaMemset(h->p, 0, fld);
+  if (h->p2) cudaMemset(h->p2, 0, fld);
   cudaMemset(h->x, 0, fld);
   cudaMemset(h->part, 0, (size_t)Lp * h->part_stride * sizeof(double));
   if (keep_u) {
@@ -257,6 +262,7 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   a.E = (const T*)h->Ein;
   a.lcs = h->lcs > 0 ? h->lcs : L;
   a.x = (T*)h->x; a.r = (T*)h->r; a.p = (T*)h->p;
+  a.p2 = h->op_form == RVE_FORM_FACTORED ? (T*)h->p2 : nullptr;
   a.in = (const T*)h->fbuf; a.out = (T*)h->fbuf;
   a.u64 = u;
   a.spec = (cplx<T>*)h->spec; a.spec2 = (cplx<T>*)h->spec2;
@@ -312,6 +318,34 @@ template <typename T> cudaError_t apply_passes(rve_s* h, const PassArgs<T>& a) {
   if (e == cudaSuccess) e = pass_mid<T>(h, a);
   if (e == cudaSuccess) e = pass_e<T>(h, a);
   return e;
+}
+
+// One projected-CG iteration in the factored nodal form:
+//   force stencil (p update, material, f = B_r^T C p, alpha)
+//   -> FFT passes on the D nodal components with w^ = (B^H B)^-1 f^
+//   -> strain update (q = B_r w, r -= alpha q, beta).
+// Iteration parity q writes the direction to {p, p2}[q] and reads the previous
+// one from the other buffer.  f and w are carved out of fbuf (idle during CG).
+template <typename T> cudaError_t apply_factored(rve_s* h, const PassArgs<T>& a, int parity) {
+  T* P[2] = {(T*)h->p, (T*)h->p2};
+  T* f = (T*)h->fbuf;
+  T* w = f + (size_t)a.L * h->D * h->N;
+  cudaError_t e = timed(h, K_FS, [&] { return launch_force_stencil<T>(a, P[parity ^ 1], P[parity], f, h->stream); });
+  PassArgs<T> b = a;
+  b.amode = A_NODAL; b.pmode = P_SOLVE; b.emode = E_NOUT;
+  b.in = f; b.out = w;
+  if (e == cudaSuccess) e = pass_a<T>(h, b);
+  if (e == cudaSuccess) e = pass_mid<T>(h, b);
+  if (e == cudaSuccess) e = pass_e<T>(h, b);
+  if (e == cudaSuccess) e = timed(h, K_SU, [&] { return launch_strain_update<T>(a, w, h->stream); });
+  return e;
+}
+
+// The k-th CG iteration of a batch (k counts from 0 at the start of an inner
+// solve; batches hold an even number of iterations, so k's parity is the
+// parity of the CG iteration count of every slot still running).
+template <typename T> cudaError_t cg_iteration(rve_s* h, const PassArgs<T>& a, int k) {
+  return h->op_form == RVE_FORM_FACTORED ? apply_factored<T>(h, a, k & 1) : apply_passes<T>(h, a);
 }
 
 int read_state(rve_s* h, int L) {
@@ -423,7 +457,7 @@ template <typename T> struct CgRunner {
       }
       h->capturing = &recs[b];
       cudaError_t e = cudaSuccess;
-      for (int k = 0; k < K && e == cudaSuccess; ++k) e = apply_passes<T>(h, a);
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = cg_iteration<T>(h, a, k);
       h->capturing = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess || !g || cudaGraphInstantiate(&exec[b], g, 0) != cudaSuccess) {
@@ -454,7 +488,7 @@ template <typename T> struct CgRunner {
     if (exec[b]) {
       e = cudaGraphLaunch(exec[b], h->stream);
     } else {
-      for (int k = 0; k < K && e == cudaSuccess; ++k) e = apply_passes<T>(h, a);
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = cg_iteration<T>(h, a, k);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(host[b], h->cg, (size_t)L * sizeof(CgState), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(copied[b], h->stream);
@@ -517,7 +551,7 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
 
   Fp64Args fa = fp64_args(h, L, u_out, emac_dev, h->cg);
   PassArgs<T> a = pass_args<T>(h, L, u_out, emac_dev);
-  const int check_every = 8;
+  const int check_every = 8;  // even: the factored form alternates its direction buffers
   std::unique_ptr<CgRunner<T>> runner;  // built at the first inner solve, reused by later ones
 
   for (int step = 0;; ++step) {
@@ -1066,6 +1100,25 @@ int rve_set_schedule(rve_t h, const int* variants) {
     if (variants[w] < -1 || variants[w] > 2) return RVE_ERR_ARG;
   h->var[0] = variants[0];
   h->var[1] = variants[1];
+  return RVE_OK;
+}
+
+int rve_set_operator_form(rve_t h, int form) {
+  if (!h || (form != RVE_FORM_STRESS && form != RVE_FORM_FACTORED)) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
+  CK(cudaStreamSynchronize(h->stream));
+  if (form == RVE_FORM_FACTORED && h->Lcap > 0 && !h->p2) {
+    const size_t fld = (size_t)h->Lcap * h->m * h->N * h->tsize;
+    if (int rc = dev_alloc(&h->p2, fld)) return rc;
+    CK(cudaMemset(h->p2, 0, fld));
+  }
+  h->op_form = form;
+  return RVE_OK;
+}
+
+int rve_operator_form(rve_t h, int* form) {
+  if (!h || !form) return RVE_ERR_ARG;
+  *form = h->op_form;
   return RVE_OK;
 }
 

@@ -21,13 +21,15 @@ enum PassEMode {
   E_CG = 0,      // r -= alpha q ; <r, r> -> beta, convergence
   E_INIT = 1,    // r = -q ; x = 0 ; <r, r> -> rr0
   E_OUT = 2,     // out = q (m components)
-  E_NODAL = 3    // u64 += q (D nodal components, accumulated in FP64)
+  E_NODAL = 3,   // u64 += q (D nodal components, accumulated in FP64)
+  E_NOUT = 4     // out = q (D nodal components, inner precision)
 };
 // Modes of the projection pass
 enum ProjMode {
   P_G = 0,       // eps^ = B (B^H B)^-1 B^H sigma^  (m -> m)
   P_NODAL_IN = 1,  // eps^ = B (B^H B)^-1 f^          (D -> m)
-  P_NODAL_OUT = 2  // u^ = (B^H B)^-1 B^H eps^        (m -> D)
+  P_NODAL_OUT = 2, // u^ = (B^H B)^-1 B^H eps^        (m -> D)
+  P_SOLVE = 3      // w^ = (B^H B)^-1 f^              (D -> D, factored form)
 };
 
 // Everything a pass kernel needs; all pointers are device pointers.
@@ -39,6 +41,7 @@ template <typename T> struct PassArgs {
   const T* E;        // [L / lcs][N] Young's modulus (one field per material)
   int lcs;           // load-case slots per material: slot l uses field l / lcs
   T* x; T* r; T* p;  // [L][m][N] CG vectors
+  T* p2;             // second direction buffer of the factored form (p alternates p, p2), else null
   const T* in;       // [L][m or D][N] input field (A_FIELD / A_BARE / A_NODAL)
   T* out;            // [L][m][N] output field (E_OUT)
   double* u64;       // [L][D][N] FP64 nodal displacement (E_NODAL)
@@ -84,6 +87,10 @@ template <typename T> cudaError_t launch_pass_c_2d(const PassArgs<T>& a, cudaStr
 template <typename T> cudaError_t launch_pass_e_2d(const PassArgs<T>& a, cudaStream_t s);
 
 template <typename T> cudaError_t launch_cg_finish_x(const PassArgs<T>& a, cudaStream_t s);
+// factored nodal form of the operator
+template <typename T>
+cudaError_t launch_force_stencil(const PassArgs<T>& a, const T* pold, T* pnew, T* f, cudaStream_t s);
+template <typename T> cudaError_t launch_strain_update(const PassArgs<T>& a, const T* w, cudaStream_t s);
 
 template <typename T> cudaError_t launch_pass_a_3d(const PassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_pass_b_3d(const PassArgs<T>& a, cudaStream_t s);
