@@ -79,6 +79,22 @@ def model_bytes(dim, n, s, L_iters, form="stress"):
     m = nq * ns
     N = int(np.prod(n))
     kx = n[0] // 2 + 1
+    if form == "nodal":
+        # force kernel: reads rho, pi_old, xi, E; writes pi, xi, f.  FFT passes on
+        # D components.  Update: reads rho_old, w; writes rho.
+        D = dim
+        specd = D * kx * (N // n[0]) * 2 * s
+        out = {
+            "force_stencil": (6 * D + 1) * N * s,
+            "pass_a": D * N * s + specd,
+            "pass_c": 2 * specd,
+            "pass_e": specd + D * N * s,
+            "strain_update": 3 * D * N * s,
+        }
+        if dim == 3:
+            out["pass_b"] = 2 * specd
+            out["pass_d"] = 2 * specd
+        return out
     if form == "factored":
         D = dim
         specd = D * kx * (N // n[0]) * 2 * s
@@ -399,25 +415,25 @@ def run_gpu(args):
             extras["fp64_gpu_solve"] = {"ms_per_solve": t64 * 1e3, "speedup_of_mixed": t64 * 1e3 / ms_step,
                                         "iterations": [i["iterations"] for i in info64],
                                         "mixed_vs_fp64_rel_diff": d64}
-        # the other order of the same operator, same workload and tolerance
-        other = "factored" if args.form == "stress" else "stress"
-        with RVE(n, precision=prec, stream=stream.cuda_stream) as ro:
-            ro.set_operator_form(other)
-            ro.set_material(E_dev, nu)
-            ro.solve(Em, rel_tol=tol, max_iter=max_iter)          # warm-up (and autotune)
-            torch.cuda.synchronize()
-            eo0, eo1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            eo0.record(stream)
-            codeo, infoo = ro.solve(Em, rel_tol=tol, max_iter=max_iter)
-            Co = ro.effective_tangent() if L == ns else ro.mean_stress()
-            eo1.record(stream)
-            torch.cuda.synchronize()
-            t_o = eo0.elapsed_time(eo1)
-        its_o = [i["iterations"] for i in infoo]
-        extras[f"{other}_form_solve"] = {
-            "ms_per_solve": t_o, "ratio_to_headline": t_o / ms_step, "iterations": its_o,
-            "ms_per_cg_iteration": t_o / max(its_o),
-            "rel_diff_to_headline": float(np.abs(C - Co).max() / np.abs(Co).max())}
+        # the other orders of the same operator, same workload and tolerance
+        for other in [f for f in ("stress", "factored", "nodal") if f != args.form]:
+            with RVE(n, precision=prec, stream=stream.cuda_stream) as ro:
+                ro.set_operator_form(other)
+                ro.set_material(E_dev, nu)
+                ro.solve(Em, rel_tol=tol, max_iter=max_iter)          # warm-up (and autotune)
+                torch.cuda.synchronize()
+                eo0, eo1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                eo0.record(stream)
+                codeo, infoo = ro.solve(Em, rel_tol=tol, max_iter=max_iter)
+                Co = ro.effective_tangent() if L == ns else ro.mean_stress()
+                eo1.record(stream)
+                torch.cuda.synchronize()
+                t_o = eo0.elapsed_time(eo1)
+            its_o = [i["iterations"] for i in infoo]
+            extras[f"{other}_form_solve"] = {
+                "ms_per_solve": t_o, "ratio_to_headline": t_o / ms_step, "iterations": its_o,
+                "ms_per_cg_iteration": t_o / max(its_o), "status": codeo,
+                "rel_diff_to_headline": float(np.abs(C - Co).max() / np.abs(Co).max())}
         # cuFFT (through torch.fft) on the same fields: context only, not part of the product
         m = (2 if dim == 2 else 6) * ns
         shape = (L * m,) + tuple(reversed(n))
@@ -483,7 +499,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
                     help="force the tile variants of passes A and E, e.g. 0,0 (default: autotune)")
-    ap.add_argument("--form", default="stress", choices=["stress", "factored"],
+    ap.add_argument("--form", default="stress", choices=["stress", "factored", "nodal"],
                     help="order of the operator inside CG (same operator; see include/rve.h)")
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the FP64 GPU solve and cuFFT timings (context figures)")

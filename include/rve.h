@@ -177,10 +177,21 @@ int rve_set_schedule(rve_t h, const int* variants);
  *                     and the strains of Eq. small-strain are formed back in
  *                     real space with the same stencils.  It needs one more
  *                     direction field [L][m][N] of the inner precision.
+ *   RVE_FORM_NODAL    the factored chain with the CG vectors themselves kept
+ *                     as nodal fields: every iterate of the projected CG is
+ *                     compatible, x = B xi, r = B rho, p = B pi, so CG runs on
+ *                     D components per node (xi, rho, pi) with the inner
+ *                     products taken in strain space (<B pi, C B pi>,
+ *                     |B rho|^2) and the same alpha, beta, stopping test and
+ *                     iterates in exact arithmetic; the strain field is
+ *                     recovered as E + B u.  This is the reading of the
+ *                     projection as a preconditioner of the FE stiffness that
+ *                     Sec. 4 points to.  No extra memory.
  * rve_set_operator_form applies from the next solve; returns RVE_ERR_ARG for
  * an unknown form, RVE_ERR_OOM if the extra field cannot be allocated. */
 #define RVE_FORM_STRESS 0
 #define RVE_FORM_FACTORED 1
+#define RVE_FORM_NODAL 2
 int rve_set_operator_form(rve_t h, int form);
 int rve_operator_form(rve_t h, int* form);
 

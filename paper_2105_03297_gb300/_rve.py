@@ -223,11 +223,12 @@ class RVE:
         v = (C.c_int * 2)(int(var_a), int(var_e))
         _check(load().rve_set_schedule(self.h, v), "rve_set_schedule")
 
-    FORMS = {"stress": 0, "factored": 1}
+    FORMS = {"stress": 0, "factored": 1, "nodal": 2}
 
     def set_operator_form(self, form):
-        """'stress' (default: FFT of every stress component) or 'factored'
-        (real-space nodal forces, FFT of the D nodal components only)."""
+        """'stress' (default: FFT of every stress component), 'factored'
+        (real-space nodal forces, FFT of the D nodal components only) or
+        'nodal' (the factored chain with the CG vectors kept as nodal fields)."""
         _check(load().rve_set_operator_form(self.h, self.FORMS[form]), "rve_set_operator_form")
 
     def operator_form(self):

@@ -141,7 +141,7 @@ __device__ __forceinline__ void project_3d(cplx<T>* col, const cplx<T>* e, const
   }
   const T r2 = (T)kInvSqrt2;
   C t3[3];
-  if (mode == P_NODAL_IN) {
+  if (mode == P_NODAL_IN || mode == P_SOLVE) {
     t3[0] = col[0]; t3[1] = col[LD]; t3[2] = col[2 * LD];
   } else {
     // t = B^H s: t_j = sum_t sum_a conj(g_ta) sigma_t,aj
@@ -172,7 +172,7 @@ __device__ __forceinline__ void project_3d(cplx<T>* col, const cplx<T>* e, const
   w[0] = cscale(cadd(cadd(cscale(t3[0], A00), cmul(A01, t3[1])), cmul(A02, t3[2])), id);
   w[1] = cscale(cadd(cadd(cjmul(A01, t3[0]), cscale(t3[1], A11)), cmul(A12, t3[2])), id);
   w[2] = cscale(cadd(cadd(cjmul(A02, t3[0]), cjmul(A12, t3[1])), cscale(t3[2], A22)), id);
-  if (mode == P_NODAL_OUT) {
+  if (mode == P_NODAL_OUT || mode == P_SOLVE) {
     col[0] = w[0]; col[LD] = w[1]; col[2 * LD] = w[2];
     return;
   }
@@ -338,6 +338,44 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
   else fft4<T, NZ, 3, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
 }
 
+// Pass C for the nodal solve w^ = (B^H B)^-1 f^ (P_SOLVE, 3 components in
+// and out): P pencils (k_x, k_y0 + i), i < P, per block, so that a block has
+// as many transforms as the 36-component pass.  Row b of the buffer is
+// component b % 3 of pencil b / 3.  grid (n_x/2+1, n_y/P, L).
+template <typename T, int NZ, int P, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d_nodal(PassArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int M = 36, R = 3 * P;
+  constexpr int LD = FftSplit<NZ>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [R][LD]
+  const int kx = blockIdx.x, ky0 = blockIdx.y * P, l = blockIdx.z;
+  const int ny = a.n[1], KX = a.kx;
+  CgState* cg = a.cg + l;
+  if (!cg->active) return;
+  if (a.cgphase && cg->status != ST_RUN) return;
+  const int64_t stride_c = (int64_t)KX * ny * NZ;
+  C* base = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky0) * NZ;
+  auto ld_g = [&](int b, int z) -> C { return base[(b % 3) * stride_c + (b / 3) * NZ + z]; };
+  auto st_s = [&](int b, int k, C v) { buf[b * LD + k] = v; };
+  fft4<T, NZ, R, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
+  for (int i = threadIdx.x; i < P * NZ; i += NT) {
+    const int pc = i / NZ, kz = i % NZ;
+    C* col = buf + 3 * pc * LD + kz;
+    if (kx == 0 && ky0 + pc == 0 && kz == 0) {
+      // k = 0: the nodal solve has no mean (w^(0) = 0)
+      col[0] = col[LD] = col[2 * LD] = mkc<T>(0, 0);
+    } else {
+      const C e[3] = {a.ph[0][kx], a.ph[1][ky0 + pc], a.ph[2][kz]};
+      project_3d<T, LD>(col, e, a.ih, a.inv_n, P_SOLVE);
+    }
+  }
+  __syncthreads();
+  auto ld_s = [&](int b, int z) -> C { return buf[b * LD + z]; };
+  auto st_g = [&](int b, int k, C v) { base[(b % 3) * stride_c + (b / 3) * NZ + k] = v; };
+  fft4<T, NZ, R, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
+}
+
 // ---------------------------------------------------------------- pass E
 // grid (n_y/TY, n_z, L*G): G = 6 tetrahedra (6 components each) or one group
 // of the 3 nodal components (E_NODAL); inverse real FFT along x and update.
@@ -457,6 +495,17 @@ template <typename T, int NY> cudaError_t launch_yb_3d_n(const PassArgs<T>& a, c
 }
 template <typename T, int NZ>
 cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if (a.pmode == P_SOLVE) {
+    constexpr int P = 8;  // n_y >= 16
+    constexpr int NTn = fft_threads<NZ, 3 * P>();
+    const size_t smn = sizeof(cplx<T>) * 3 * P * FftSplit<NZ>::LD;
+    auto kn = pass_c_3d_nodal<T, NZ, P, NTn>;
+    static bool attr_n = false;
+    if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
+    dim3 gridn(a.kx, a.n[1] / P, a.L);
+    kn<<<gridn, NTn, smn, s>>>(a);
+    return cudaGetLastError();
+  }
   constexpr int NT = fft_threads<NZ, 36>();
   const size_t sm = sizeof(cplx<T>) * 36 * FftSplit<NZ>::LD;
   auto k = pass_c_3d<T, NZ, NT>;

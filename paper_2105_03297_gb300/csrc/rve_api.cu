@@ -341,11 +341,45 @@ template <typename T> cudaError_t apply_factored(rve_s* h, const PassArgs<T>& a,
   return e;
 }
 
+// Nodal-state buffers: xi, rho[2], pi[2], f, w, each [L][D][N] of the inner
+// precision, carved out of the strain-form fields (m >= 2 D components).
+template <typename T> struct NodalBufs {
+  T* xi; T* rho[2]; T* pi[2]; T* f; T* w;
+  NodalBufs(const rve_s* h, int L) {
+    const size_t nd = (size_t)L * h->D * h->N;
+    xi = (T*)h->x;
+    rho[0] = (T*)h->r; rho[1] = rho[0] + nd;
+    pi[0] = (T*)h->p; pi[1] = pi[0] + nd;
+    f = (T*)h->fbuf; w = f + nd;
+  }
+};
+
+// One projected-CG iteration on the nodal state (parity q of the iteration):
+// force kernel (pi, xi, f = B^T C B pi, alpha) -> FFT passes with
+// w^ = (B^H B)^-1 f^ -> update kernel (rho -= alpha w, <B rho, B rho>, beta).
+template <typename T> cudaError_t apply_nodal(rve_s* h, const PassArgs<T>& a, int q) {
+  NodalBufs<T> nb(h, a.L);
+  cudaError_t e = timed(h, K_FS, [&] {
+    return launch_nodal_force<T>(a, nb.rho[q], nb.pi[q ^ 1], nb.pi[q], nb.xi, nb.f, h->stream);
+  });
+  PassArgs<T> b = a;
+  b.amode = A_NODAL; b.pmode = P_SOLVE; b.emode = E_NOUT;
+  b.in = nb.f; b.out = nb.w;
+  if (e == cudaSuccess) e = pass_a<T>(h, b);
+  if (e == cudaSuccess) e = pass_mid<T>(h, b);
+  if (e == cudaSuccess) e = pass_e<T>(h, b);
+  if (e == cudaSuccess)
+    e = timed(h, K_SU, [&] { return launch_nodal_update<T>(a, nb.rho[q], nb.w, nb.rho[q ^ 1], nb.xi, 0, h->stream); });
+  return e;
+}
+
 // The k-th CG iteration of a batch (k counts from 0 at the start of an inner
 // solve; batches hold an even number of iterations, so k's parity is the
 // parity of the CG iteration count of every slot still running).
 template <typename T> cudaError_t cg_iteration(rve_s* h, const PassArgs<T>& a, int k) {
-  return h->op_form == RVE_FORM_FACTORED ? apply_factored<T>(h, a, k & 1) : apply_passes<T>(h, a);
+  if (h->op_form == RVE_FORM_FACTORED) return apply_factored<T>(h, a, k & 1);
+  if (h->op_form == RVE_FORM_NODAL) return apply_nodal<T>(h, a, k & 1);
+  return apply_passes<T>(h, a);
 }
 
 int read_state(rve_s* h, int L) {
@@ -592,16 +626,31 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
       h->cg_h[l].cnt_a = h->cg_h[l].cnt_e = h->cg_h[l].cnt_r = 0;
     }
     if ((rc = write_state(h, L))) return rc;
-    // inner right-hand side r0 = -G C (E + B u) from f
-    a.cgphase = 0; a.amode = A_NODAL; a.pmode = P_NODAL_IN; a.emode = E_INIT;
-    a.in = (const T*)h->fbuf;
-    CK(apply_passes<T>(h, a));
+    // inner right-hand side r0 = -G C (E + B u) from f (nodal state: rho0 = -K^-1 f)
+    a.cgphase = 0;
+    if (h->op_form == RVE_FORM_NODAL) {
+      NodalBufs<T> nb(h, L);
+      PassArgs<T> b = a;
+      b.amode = A_NODAL; b.pmode = P_SOLVE; b.emode = E_NOUT;
+      b.in = nb.f; b.out = nb.w;
+      CK(apply_passes<T>(h, b));
+      CK(timed(h, K_OTHER, [&] { return launch_nodal_update<T>(a, nullptr, nb.w, nb.rho[0], nb.xi, 1, h->stream); }));
+    } else {
+      a.amode = A_NODAL; a.pmode = P_NODAL_IN; a.emode = E_INIT;
+      a.in = (const T*)h->fbuf;
+      CK(apply_passes<T>(h, a));
+    }
     // projected CG
     a.cgphase = 1; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
     if (!runner) runner.reset(new CgRunner<T>(h, L, a, check_every));
     if ((rc = runner->run(active, (max_iter + check_every - 1) / check_every + 1))) return rc;
-    // apply the x update the last iteration deferred
-    CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<T>(a, h->stream); }));
+    // apply the x update the last iteration deferred (nodal state: and u += xi)
+    if (h->op_form == RVE_FORM_NODAL) {
+      NodalBufs<T> nb(h, L);
+      CK(timed(h, K_OTHER, [&] { return launch_nodal_finish<T>(a, nb.pi[0], nb.pi[1], nb.xi, h->stream); }));
+    } else {
+      CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<T>(a, h->stream); }));
+    }
     if ((rc = read_state(h, L))) return rc;
     for (int l = 0; l < L; ++l) {
       if (!active[l]) continue;
@@ -610,10 +659,12 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
       cgrel[l] = h->cg_h[l].rr0 > 0 ? std::sqrt(h->cg_h[l].rr / h->cg_h[l].rr0) : 0.0;
       if (h->cg_h[l].status == ST_BAD) bad[l] = 1;
     }
-    // u += (B^H B)^-1 B^H delta  (delta = CG iterate x)
-    a.cgphase = 0; a.amode = A_BARE; a.pmode = P_NODAL_OUT; a.emode = E_NODAL;
-    a.in = (const T*)h->x;
-    CK(apply_passes<T>(h, a));
+    // u += (B^H B)^-1 B^H delta  (delta = CG iterate x; the nodal state added xi above)
+    if (h->op_form != RVE_FORM_NODAL) {
+      a.cgphase = 0; a.amode = A_BARE; a.pmode = P_NODAL_OUT; a.emode = E_NODAL;
+      a.in = (const T*)h->x;
+      CK(apply_passes<T>(h, a));
+    }
     for (int l = 0; l < L; ++l)
       if (bad[l]) { active[l] = 0; h->cg_h[l].active = 0; }
     if ((rc = write_state(h, L))) return rc;
@@ -1104,7 +1155,7 @@ int rve_set_schedule(rve_t h, const int* variants) {
 }
 
 int rve_set_operator_form(rve_t h, int form) {
-  if (!h || (form != RVE_FORM_STRESS && form != RVE_FORM_FACTORED)) return RVE_ERR_ARG;
+  if (!h || (form != RVE_FORM_STRESS && form != RVE_FORM_FACTORED && form != RVE_FORM_NODAL)) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   CK(cudaStreamSynchronize(h->stream));
   if (form == RVE_FORM_FACTORED && h->Lcap > 0 && !h->p2) {

@@ -91,6 +91,16 @@ template <typename T> cudaError_t launch_cg_finish_x(const PassArgs<T>& a, cudaS
 template <typename T>
 cudaError_t launch_force_stencil(const PassArgs<T>& a, const T* pold, T* pnew, T* f, cudaStream_t s);
 template <typename T> cudaError_t launch_strain_update(const PassArgs<T>& a, const T* w, cudaStream_t s);
+// nodal-state form
+template <typename T>
+cudaError_t launch_nodal_force(const PassArgs<T>& a, const T* rho, const T* pold, T* pnew, T* xi, T* f,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_nodal_update(const PassArgs<T>& a, const T* rho_old, const T* w, T* rho_new, T* xi, int init,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_nodal_finish(const PassArgs<T>& a, const T* pi_even, const T* pi_odd, const T* xi,
+                                cudaStream_t s);
 
 template <typename T> cudaError_t launch_pass_a_3d(const PassArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_pass_b_3d(const PassArgs<T>& a, cudaStream_t s);
