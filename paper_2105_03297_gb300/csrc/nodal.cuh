@@ -498,45 +498,65 @@ __global__ void __launch_bounds__(kMNT) nodal_force_2d(PassArgs<T> a, const T* _
   }
 }
 
+// 2D counterpart of nodal_update_3d: NT threads cover bx columns (bx =
+// min(n_x, NT)) x NT/bx row groups of kUY rows; each thread sweeps its rows
+// keeping the updated corner values of row y + 1.  grid (n_x/bx,
+// max(1, n_y/(kUY NT/bx)) L); row groups past n_y are idle.
+constexpr int kUY = 16;
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) nodal_update_2d(PassArgs<T> a, const T* __restrict__ rho_old,
                                                       const T* __restrict__ w, T* __restrict__ rho_new,
                                                       T* __restrict__ xi, int init) {
   __shared__ double red[NT / 32];
   __shared__ int flag;
-  const int l = blockIdx.y;
+  const int nx = a.n[0], ny = a.n[1];
+  const int bx = nx < NT ? nx : NT, by = NT / bx;
+  const int rows_blk = by * kUY;
+  const int nyb = ny > rows_blk ? ny / rows_blk : 1;
+  const int l = blockIdx.y / nyb, yb = blockIdx.y % nyb;
   CgState* cg = a.cg + l;
   if (!cg->active) return;
   if (a.cgphase && cg->status != ST_RUN) return;
-  const int nx = a.n[0], ny = a.n[1];
   const int64_t N = a.N;
-  const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int x = blockIdx.x * bx + (threadIdx.x % bx);
+  const int ys = yb * rows_blk + (threadIdx.x / bx) * kUY;
+  const int x1 = (x + 1) & (nx - 1);
   const T alpha = init ? (T)0 : (T)cg->alpha;
   const int64_t lbase = (int64_t)l * 2 * N;
   T acc = 0;
-  if (v < N) {
-    const int x = (int)(v % nx), y = (int)(v / nx);
-    T uc[4][2];
+  if (ys < ny) {
+    auto corners = [&](int y, T c[2][2]) {
+      const int64_t rb = lbase + (int64_t)(y & (ny - 1)) * nx;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int cx = (x + (c & 1)) & (nx - 1), cy = (y + (c >> 1)) & (ny - 1);
-      const int64_t i = lbase + (int64_t)cy * nx + cx;
+      for (int j = 0; j < 2; ++j) {
+        const int64_t i0 = rb + (int64_t)j * N + x, i1 = rb + (int64_t)j * N + x1;
+        c[0][j] = init ? -__ldg(w + i0) : __ldg(rho_old + i0) - alpha * __ldg(w + i0);
+        c[1][j] = init ? -__ldg(w + i1) : __ldg(rho_old + i1) - alpha * __ldg(w + i1);
+      }
+    };
+    T lo[2][2], hi[2][2];
+    corners(ys, lo);
+    for (int y = ys; y < ys + kUY; ++y) {
+      corners(y + 1, hi);
+      const int64_t v = lbase + (int64_t)y * nx + x;
+      rho_new[v] = lo[0][0];
+      rho_new[v + N] = lo[0][1];
+      if (init) { xi[v] = 0; xi[v + N] = 0; }
+      const T uc[4][2] = {{lo[0][0], lo[0][1]}, {lo[1][0], lo[1][1]}, {hi[0][0], hi[0][1]}, {hi[1][0], hi[1][1]}};
+      T q[6];
+      tri_strains_2d<T>(uc, a.ih[0], a.ih[1], q);
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
-        uc[c][j] = init ? -__ldg(w + i + j * N) : __ldg(rho_old + i + j * N) - alpha * __ldg(w + i + j * N);
+      for (int c = 0; c < 6; ++c) acc += q[c] * q[c];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) { lo[k][0] = hi[k][0]; lo[k][1] = hi[k][1]; }
     }
-    rho_new[lbase + v] = uc[0][0];
-    rho_new[lbase + N + v] = uc[0][1];
-    if (init) { xi[lbase + v] = 0; xi[lbase + N + v] = 0; }
-    T q[6];
-    tri_strains_2d<T>(uc, a.ih[0], a.ih[1], q);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc += q[c] * q[c];
   }
   const double s = block_sum<NT>((double)acc, red);
+  const int nblk = gridDim.x * nyb;
+  const int blk = blockIdx.x + gridDim.x * yb;
   double* part = a.part + (int64_t)l * a.part_stride;
-  if (publish_partial(s, part, &cg->cnt_e, blockIdx.x, gridDim.x, &flag)) {
-    const double rr = sum_partials<NT>(part, gridDim.x, red);
+  if (publish_partial(s, part, &cg->cnt_e, blk, nblk, &flag)) {
+    const double rr = sum_partials<NT>(part, nblk, red);
     if (threadIdx.x == 0) finish_rr(cg, rr, init != 0);
   }
 }
@@ -595,7 +615,9 @@ cudaError_t launch_nodal_update(const PassArgs<T>& a, const T* rho_old, const T*
     dim3 grid(a.n[0] / bx, a.n[1] / by, (a.n[2] / tz) * a.L);
     nodal_update_3d<T, NT><<<grid, NT, 0, s>>>(a, rho_old, w, rho_new, xi, init);
   } else {
-    dim3 grid((unsigned)((a.N + NT - 1) / NT), a.L);
+    const int bx = a.n[0] < NT ? a.n[0] : NT, rows_blk = (NT / bx) * kUY;
+    const int nyb = a.n[1] > rows_blk ? a.n[1] / rows_blk : 1;
+    dim3 grid(a.n[0] / bx, nyb * a.L);
     nodal_update_2d<T, NT><<<grid, NT, 0, s>>>(a, rho_old, w, rho_new, xi, init);
   }
   return cudaGetLastError();

@@ -340,6 +340,51 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs
   else fft4<T, NY, 2, LD, NT, +1, true, false, false, false>(buf, a.tw[1], ld_s, st_g);
 }
 
+// Pass C for the nodal solve w^ = (B^H B)^-1 f^ (P_SOLVE, 2 components in and
+// out): P k_x columns per block so that a block holds as many transforms as
+// the 6-component pass.  Row b is component b % 2 of column kx0 + b / 2;
+// columns past n_x/2 are skipped.  grid (ceil((n_x/2+1) / P), L).
+template <typename T, int NY, int P, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d_nodal(PassArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int M = 6, R = 2 * P;
+  constexpr int LD = FftSplit<NY>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [R][LD]
+  const int kx0 = blockIdx.x * P, l = blockIdx.y;
+  const int KX = a.kx;
+  CgState* cg = a.cg + l;
+  if (!cg->active) return;
+  if (a.cgphase && cg->status != ST_RUN) return;
+  const int64_t cstride = (int64_t)KX * NY;
+  C* base = a.spec + ((int64_t)l * M * KX + kx0) * NY;
+  auto ld_g = [&](int b, int y) -> C {
+    return (kx0 + b / 2 < KX) ? base[(b % 2) * cstride + (int64_t)(b / 2) * NY + y] : mkc<T>(0, 0);
+  };
+  auto st_s = [&](int b, int k, C v) { buf[b * LD + k] = v; };
+  fft4<T, NY, R, LD, NT, -1, false, true, false, false>(buf, a.tw[1], ld_g, st_s);
+  for (int i = threadIdx.x; i < P * NY; i += NT) {
+    const int pc = i / NY, ky = i % NY, kx = kx0 + pc;
+    if (kx >= KX) continue;
+    C s2[M];
+    s2[0] = buf[2 * pc * LD + ky];
+    s2[1] = buf[(2 * pc + 1) * LD + ky];
+    if (kx == 0 && ky == 0) {
+      s2[0] = s2[1] = mkc<T>(0, 0);   // k = 0: the nodal solve has no mean
+    } else {
+      project_2d<T>(s2, a.ph[0][kx], a.ph[1][ky], a.ih[0], a.ih[1], a.inv_n, P_SOLVE);
+    }
+    buf[2 * pc * LD + ky] = s2[0];
+    buf[(2 * pc + 1) * LD + ky] = s2[1];
+  }
+  __syncthreads();
+  auto ld_s = [&](int b, int y) -> C { return buf[b * LD + y]; };
+  auto st_g = [&](int b, int k, C v) {
+    if (kx0 + b / 2 < KX) base[(b % 2) * cstride + (int64_t)(b / 2) * NY + k] = v;
+  };
+  fft4<T, NY, R, LD, NT, +1, true, false, false, false>(buf, a.tw[1], ld_s, st_g);
+}
+
 // ------------------------------------------------------------------------
 // Pass E body shared by 2D and 3D: load the (k, y-pair) spectra of ge
 // components into packed rows (component j at src + j*comp_stride +
@@ -566,6 +611,17 @@ cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
 }
 template <typename T, int NY>
 cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if (a.pmode == P_SOLVE) {
+    constexpr int P = 3;
+    constexpr int NTn = fft_threads<NY, 2 * P>();
+    const size_t smn = sizeof(cplx<T>) * 2 * P * FftSplit<NY>::LD;
+    auto kn = pass_c_2d_nodal<T, NY, P, NTn>;
+    static bool attr_n = false;
+    if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
+    dim3 gridn((a.kx + P - 1) / P, a.L);
+    kn<<<gridn, NTn, smn, s>>>(a);
+    return cudaGetLastError();
+  }
   constexpr int NT = fft_threads<NY, 6>();
   const size_t sm = sizeof(cplx<T>) * 6 * FftSplit<NY>::LD;
   auto k = pass_c_2d<T, NY, NT>;
