@@ -101,8 +101,14 @@ int rve_create(rve_t* out, int dim, const int64_t* n, const double* length,
 int rve_destroy(rve_t h);
 
 /* Set the material: per-voxel Young's modulus E[N] (dtype RVE_F32/RVE_F64,
- * must be finite and > 0) and the Poisson ratio nu in (-1, 0.5)
- * (isotropic small-strain Hooke's law, Sec. 3.3; plane strain in 2D). */
+ * finite and >= 0, not all zero) and the Poisson ratio nu in (-1, 0.5)
+ * (isotropic small-strain Hooke's law, Sec. 3.3; plane strain in 2D).
+ * E = 0 is a zero-stiffness (vacuum) voxel (Sec. 3.2): the projected operator
+ * is then only semi-definite and CG runs on its range.  The mean stresses,
+ * C_eff and the strains of every element with E > 0 are unique (the energy is
+ * strictly convex in them); strains of zero-stiffness elements, and the
+ * adjoint gradient at zero-stiffness voxels, can carry any null-space
+ * component and are not. */
 int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_flags);
 
 /* Solve L load cases together.  E_macro[L][n_s] (host, Mandel) are the

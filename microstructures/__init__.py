@@ -130,6 +130,50 @@ def laminate(n, layer_moduli):
     return np.broadcast_to(layer_moduli, array_shape(n)).copy()
 
 
+def porous_lognormal(n, void_fraction=0.25, sigma=1.0, seed=1008):
+    """Log-normal moduli with a random set of zero-stiffness (vacuum) voxels.
+
+    Every voxel is independently void with probability ``void_fraction``
+    (E = 0); the others get ``exp(N(0, sigma^2))``.
+    """
+    rng = np.random.default_rng(seed)
+    E = np.exp(sigma * rng.standard_normal(array_shape(n)))
+    E[rng.random(array_shape(n)) < void_fraction] = 0.0
+    return E
+
+
+def two_pillars(n, gaps=(None, None), E_hard=1.0, soft_ratio=0.1, inclusion=3):
+    """Two stiff pillars (bands normal to x) separated by two single-voxel
+    zero-stiffness columns, in the spirit of the vacuum example (Sec. 3.2).
+
+    Columns ``gaps`` (default n_x/2 - 1 and n_x - 1) have E = 0, which cuts the
+    periodic cell into two bodies: pillar A (x < gaps[0]) and pillar B.
+    Pillar A holds a centred square soft inclusion of ``inclusion`` voxels per
+    side with E = soft_ratio * E_hard.  Returns (E, mask_A, mask_B).
+    """
+    nx = n[0]
+    g0 = nx // 2 - 1 if gaps[0] is None else gaps[0]
+    g1 = nx - 1 if gaps[1] is None else gaps[1]
+    shape = array_shape(n)
+    E = np.full(shape, float(E_hard))
+    ix = np.arange(nx)
+    E[..., ix == g0] = 0.0
+    E[..., ix == g1] = 0.0
+    maskA = np.broadcast_to(ix < g0, shape).copy()
+    maskB = np.broadcast_to((ix > g0) & (ix < g1), shape).copy()
+    # soft inclusion at the centre of pillar A (in every z plane for 3D: a fibre)
+    cx = g0 // 2
+    lo = cx - inclusion // 2
+    sl_x = slice(lo, lo + inclusion)
+    ny = n[1]
+    sl_y = slice(ny // 2 - inclusion // 2, ny // 2 - inclusion // 2 + inclusion)
+    if len(n) == 2:
+        E[sl_y, sl_x] = soft_ratio * E_hard
+    else:
+        E[:, sl_y, sl_x] = soft_ratio * E_hard
+    return E, maskA, maskB
+
+
 def uneven_batch_2d(count=64, sides=(64, 128, 256, 512), sigma_px=8.0, seed=1004):
     """Batch of square 2D two-phase RVEs of uneven size.
 

@@ -34,27 +34,36 @@ def laminate_tangent(layer_E, nu, dim):
     C_yyyy = <M - lambda^2/M> + <lambda/M>^2 <1/M>^-1,
     C_yyzz = <lambda - lambda^2/M> + <lambda/M>^2 <1/M>^-1,
     x-shears (Mandel) 2 <1/mu>^-1, the in-layer shear 2 <mu>.
+    Zero-modulus layers are allowed (the series averages then vanish).
     """
-    lam, mu = lame(np.asarray(layer_E, dtype=np.float64), nu)
-    M = lam + 2.0 * mu
-    iM = np.mean(1.0 / M)
-    lM = np.mean(lam / M)
+    E = np.asarray(layer_E, dtype=np.float64)
+    # every modulus is E times its unit-modulus value, so the ratios lambda/M
+    # and lambda^2/M = E lambda1^2/M1 stay finite for zero-stiffness layers
+    # (vacuum, Sec. 3.2), where the series averages <1/M>^-1, <1/mu>^-1 -> 0
+    lam1, mu1 = lame(1.0, nu)
+    M1 = lam1 + 2.0 * mu1
+    lam, mu, M = E * lam1, E * mu1, E * M1
+    any_void = bool(np.any(E == 0.0))
+    inv_iM = 0.0 if any_void else 1.0 / np.mean(1.0 / M)
+    inv_imu = 0.0 if any_void else 1.0 / np.mean(1.0 / mu)
+    lM = lam1 / M1                       # lambda/M of every layer
+    l2M = E * lam1 ** 2 / M1             # lambda^2/M of every layer
     ns = n_strain(dim)
     C = np.zeros((ns, ns))
-    C[0, 0] = 1.0 / iM
+    C[0, 0] = inv_iM
     for t in range(1, dim):
-        C[0, t] = C[t, 0] = lM / iM
+        C[0, t] = C[t, 0] = lM * inv_iM
     for s in range(1, dim):
         for t in range(1, dim):
             if s == t:
-                C[s, t] = np.mean(M - lam ** 2 / M) + lM ** 2 / iM
+                C[s, t] = np.mean(M - l2M) + lM ** 2 * inv_iM
             else:
-                C[s, t] = np.mean(lam - lam ** 2 / M) + lM ** 2 / iM
+                C[s, t] = np.mean(lam - l2M) + lM ** 2 * inv_iM
     pairs = mandel_pairs(dim)
     for s in range(dim, ns):
         i, j = pairs[s]
         if i == 0 or j == 0:
-            C[s, s] = 2.0 / np.mean(1.0 / mu)
+            C[s, s] = 2.0 * inv_imu
         else:
             C[s, s] = 2.0 * np.mean(mu)
     return C

@@ -762,6 +762,17 @@ int alloc_materials(rve_s* h, int n_mat) {
   return RVE_OK;
 }
 
+// Moduli must be finite and >= 0 (zero-stiffness voxels model vacuum, which
+// the linear-FE projection decouples, Sec. 3.2), with at least one > 0.
+int check_moduli(const std::vector<double>& e64) {
+  bool any = false;
+  for (double v : e64) {
+    if (!(v >= 0.0) || !std::isfinite(v)) return RVE_ERR_ARG;
+    any = any || v > 0.0;
+  }
+  return any ? RVE_OK : RVE_ERR_ARG;
+}
+
 // Validated FP64 copy of a modulus field on the host.
 int read_moduli(int64_t N, const void* E, int E_dtype, int ptr_flags, std::vector<double>& e64) {
   e64.resize((size_t)N);
@@ -777,9 +788,7 @@ int read_moduli(int64_t N, const void* E, int E_dtype, int ptr_flags, std::vecto
     if (E_dtype == RVE_F64) std::memcpy(e64.data(), E, (size_t)N * sizeof(double));
     else for (int64_t i = 0; i < N; ++i) e64[i] = ((const float*)E)[i];
   }
-  for (int64_t i = 0; i < N; ++i)
-    if (!(e64[i] > 0.0) || !std::isfinite(e64[i])) return RVE_ERR_ARG;
-  return RVE_OK;
+  return check_moduli(e64);
 }
 
 // Upload field `slot` (FP64 host copy) and its inner-precision copy.
@@ -935,8 +944,7 @@ int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_fla
     if (E_dtype == RVE_F64) std::memcpy(e64.data(), E, (size_t)h->N * sizeof(double));
     else for (int64_t i = 0; i < h->N; ++i) e64[i] = ((const float*)E)[i];
   }
-  for (int64_t i = 0; i < h->N; ++i)
-    if (!(e64[i] > 0.0) || !std::isfinite(e64[i])) return RVE_ERR_ARG;
+  if (int rc = check_moduli(e64)) return rc;
   CK(cudaMemcpy(h->E64, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice));
   if (h->precision == RVE_MIXED) {
     f32_from_f64<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->E64, (float*)h->Ein, h->N);
