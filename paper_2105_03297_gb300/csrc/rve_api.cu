@@ -622,7 +622,15 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
       h->cg_h[l].status = ST_RUN;
       h->cg_h[l].it = 0;
       h->cg_h[l].maxit = max_iter - iters[l];
-      h->cg_h[l].tol2 = inner_tol * inner_tol;
+      // do not solve further than the outer tolerance needs: after a first
+      // step the residual has to fall by rel_tol / frel only (with a margin of
+      // 10 for the different norms of the inner and outer residuals).  This
+      // also keeps a later inner solve from chasing the rounding noise of its
+      // right-hand side, which with zero-stiffness regions has parts the
+      // semi-definite operator cannot reduce.
+      double tl = inner_tol;
+      if (step > 0 && frel[l] > 0.0) tl = std::fmax(tl, std::fmin(0.5, 0.1 * rel_tol / frel[l]));
+      h->cg_h[l].tol2 = tl * tl;
       h->cg_h[l].cnt_a = h->cg_h[l].cnt_e = h->cg_h[l].cnt_r = 0;
     }
     if ((rc = write_state(h, L))) return rc;
