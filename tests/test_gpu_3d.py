@@ -127,3 +127,25 @@ def test_anisotropic_voxels_3d():
         C = r.effective_tangent()
     assert code == 0, info
     assert rel_max(C, C_ref) < 1e-9
+
+
+@pytest.mark.parametrize("form", ["stress", "nodal"])
+def test_spheres128_golden(form):
+    """128^3 random non-overlapping spheres (r = 6, vf 0.2, contrast 1000), six
+    unit load cases: the mean stress of every load case whose oracle solution
+    is stored (one file per load case) to 1e-9 of the largest stored entry."""
+    parts = {l: os.path.join(GOLDEN, f"spheres128_lc{l}.json") for l in range(6)}
+    parts = {l: json.load(open(p)) for l, p in parts.items() if os.path.exists(p)}
+    if not parts:
+        pytest.skip("golden not generated")
+    from paper_2105_03297_gb300 import RVE
+    cfg = ms.config_inputs("spheres128")
+    with RVE(cfg["n"], precision="mixed") as r:
+        r.set_operator_form(form)
+        r.set_material(cfg["E"], cfg["nu"])
+        code, info = r.solve(np.eye(6), rel_tol=1e-11, max_iter=5000)
+        S = r.mean_stress()
+    assert code == 0, info
+    ref = np.array([parts[l]["mean_stress"] for l in sorted(parts)])
+    got = np.array([S[l] for l in sorted(parts)])
+    assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
