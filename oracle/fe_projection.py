@@ -127,7 +127,8 @@ def apply_material(field, E, nu):
     ``field``: (m, *array_shape) Mandel strains; ``E``: (*array_shape) moduli.
     """
     dim = E.ndim
-    ns, nq = n_strain(dim), n_elements(dim)
+    ns = n_strain(dim)
+    nq = field.shape[0] // ns
     Cbar = stiffness_mandel(dim, 1.0, nu)
     f = field.reshape((nq, ns) + E.shape)
     sig = np.einsum("st,qt...->qs...", Cbar, f) * E[None, None]
@@ -179,6 +180,80 @@ def element_gradient_symbols(n, length=None):
     return np.array(tets)
 
 
+# Other discrete derivatives of Secs. 2.3-2.5 and Appendix C, each with n_q
+# evaluation points per voxel; only B(k) changes.
+DERIVATIVES = ("fe", "fourier", "central", "forward", "lsq", "fourier2")
+
+
+def wrapped_angles(n):
+    """theta_a = k_a h_a in (-pi, pi) per axis (broadcast shapes as phase_factors);
+    the Nyquist index of an even axis gets theta = 0 (our reading of the
+    ambiguity discussed in Sec. 2.7: the average of the two grid choices)."""
+    D = len(n)
+    out = []
+    for a, na in enumerate(n):
+        m = np.arange(na)
+        w = np.where(m < (na + 1) // 2, m, m - na).astype(np.float64)
+        if na % 2 == 0:
+            w[na // 2] = 0.0
+        sh = [1] * D
+        sh[D - 1 - a] = na
+        out.append((2.0 * np.pi * w / na).reshape(sh))
+    return out
+
+
+def derivative_symbols(n, length=None, derivative="fe"):
+    """g[Theta][a](k) for the derivative ``derivative`` (shape (n_q, D, *array_shape)).
+
+    fe:       the linear finite elements (``element_gradient_symbols``), n_q = 2 / 6;
+    forward:  Eq. forward-difference-derivative-fourier, (exp(i theta_a) - 1)/h_a;
+    central:  Eq. central-difference-derivative-fourier, i sin(theta_a)/h_a;
+    lsq:      the least-squares voxel gradient of Sec. 2.5 (forward difference
+              along a averaged over the voxel edges parallel to a);
+    fourier:  i k_a = i theta_a / h_a (Eq. original-G's derivative);
+    fourier2: Appendix C, two evaluation points (2D), i k_a exp(-+ i sum_b theta_b / 6).
+    """
+    if derivative == "fe":
+        return element_gradient_symbols(n, length)
+    D = len(n)
+    h = voxel_size(n, length)
+    # phases with the exact values at theta = 0, pi/2, pi, 3pi/2, so that the
+    # derivatives that vanish there (central differences, least squares) vanish
+    # exactly rather than at the rounding level of sin(pi)
+    e = []
+    for ea in phase_factors(n):
+        ea = ea.copy()
+        ea.real[np.abs(ea.real) < 1e-14] = 0.0
+        ea.imag[np.abs(ea.imag) < 1e-14] = 0.0
+        e.append(ea)
+    th = wrapped_angles(n)
+    shp = array_shape(n)
+    one = np.ones(shp)
+    if derivative == "forward":
+        return np.array([[(e[a] - 1.0) / h[a] * one for a in range(D)]])
+    if derivative == "central":
+        # (u(x + h) - u(x - h)) / 2h -> (e - 1/e) / 2h = i sin(theta) / h
+        return np.array([[0.5 * (e[a] - 1.0 / e[a]) / h[a] * one for a in range(D)]])
+    if derivative == "lsq":
+        g = []
+        for a in range(D):
+            v = (e[a] - 1.0) / h[a] * one
+            for b in range(D):
+                if b != a:
+                    v = v * 0.5 * (1.0 + e[b])
+            g.append(v)
+        return np.array([g])
+    if derivative == "fourier":
+        return np.array([[1j * th[a] / h[a] * one for a in range(D)]])
+    if derivative == "fourier2":
+        assert D == 2, "two evaluation points are defined for 2D"
+        phi = (th[0] + th[1]) / 6.0 * one
+        ik = [1j * th[a] / h[a] * one for a in range(D)]
+        return np.array([[ik[a] * np.exp(-1j * phi) for a in range(D)],
+                         [ik[a] * np.exp(+1j * phi) for a in range(D)]])
+    raise ValueError(derivative)
+
+
 def strain_symbol(g):
     """B(k): (*array_shape, m, D) complex, Fourier symbol of u -> sym(grad_Theta u).
 
@@ -215,23 +290,28 @@ def projection_matrices(B):
 class Problem:
     """A periodic RVE: grid, cell lengths, per-voxel moduli and Poisson ratio."""
 
-    def __init__(self, n, E, nu, length=None):
+    def __init__(self, n, E, nu, length=None, derivative="fe"):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         self.E = np.asarray(E, dtype=np.float64)
         assert self.E.shape == array_shape(self.n)
         self.nu = float(nu)
         self.length = length
+        self.derivative = derivative
         self.ns = n_strain(self.dim)
-        self.nq = n_elements(self.dim)
+        self.g = derivative_symbols(self.n, length, derivative)
+        self.nq = self.g.shape[0]
         self.m = self.ns * self.nq
-        self.g = element_gradient_symbols(self.n, length)
         self.B = strain_symbol(self.g)  # (*shape, m, D)
         BH = np.conj(np.swapaxes(self.B, -1, -2))
         M = BH @ self.B
-        zero = (0,) * self.dim
-        M[zero] = np.eye(self.dim)
-        self.BHB = M  # B^H B with the k = 0 block replaced by I (never used at k = 0)
+        # G = 0 where B vanishes: k = 0 (Sec. 2.3) and, for derivatives that
+        # vanish at other wavevectors (central differences, least squares, the
+        # zeroed Nyquist of the Fourier derivative), those wavevectors too
+        self.singular = np.all(np.abs(self.B) == 0.0, axis=(-2, -1))
+        self.singular[(0,) * self.dim] = True
+        M[self.singular] = np.eye(self.dim)
+        self.BHB = M  # B^H B with the singular blocks replaced by I (never used there)
         self.axes = tuple(range(1, self.dim + 1))
 
     # -- the projection, applied in the factored form B (B^H B)^-1 B^H ----
@@ -241,7 +321,7 @@ class Problem:
         t = np.conj(np.swapaxes(self.B, -1, -2)) @ x      # B^H f
         u = np.linalg.solve(self.BHB, t)                  # (B^H B)^-1 B^H f
         y = (self.B @ u)[..., 0]                          # B (...)
-        y[(0,) * self.dim] = 0.0
+        y[self.singular] = 0.0
         return np.moveaxis(y, -1, 0)
 
     def project(self, f):
