@@ -201,6 +201,38 @@ int rve_set_schedule(rve_t h, const int* variants);
 int rve_set_operator_form(rve_t h, int form);
 int rve_operator_form(rve_t h, int* form);
 
+/* Discrete derivative of the projection (B(k) and n_q, the evaluation points
+ * per voxel).  RVE_DERIV_FE (default) is the linear-finite-element projection
+ * (Sec. 2.6: two triangles / six Kuhn tetrahedra per voxel).  The others are
+ * the comparison operators of the paper, one evaluation point per voxel unless
+ * stated:
+ *   RVE_DERIV_FOURIER   i k (Eq. original-G; on even grids the Nyquist
+ *                       component of k is taken as 0, the average of the two
+ *                       grid choices of Sec. 2.7),
+ *   RVE_DERIV_CENTRAL   central differences (Eq. central-difference-derivative-fourier),
+ *   RVE_DERIV_FORWARD   forward differences (Eq. forward-difference-derivative-fourier),
+ *   RVE_DERIV_LSQ       the least-squares voxel gradient of Sec. 2.5,
+ *   RVE_DERIV_FOURIER2  the Fourier derivative at the two triangle centroids
+ *                       (Appendix C; 2D only, n_q = 2).
+ * G = 0 wherever every symbol vanishes (k = 0; for central differences, least
+ * squares and the Fourier derivative also some Nyquist wavevectors).  The
+ * non-FE derivatives have no nodal real-space residual, so their solve is the
+ * plain projected CG on the strain fluctuation in FP64 (the handle must be
+ * RVE_FP64 and in RVE_FORM_STRESS; otherwise RVE_ERR_ARG), stopping on
+ * ||r|| <= rel_tol ||r0||; rve_adjoint and rve_energy_tangent are for
+ * RVE_DERIV_FE only.  Changing the derivative drops the handle's solution
+ * and per-load-case buffers (the strain field then has m = n_q n_s
+ * components; rve_sizes reports it); rve_apply_operator uses the handle's
+ * derivative.  rve_derivative returns the code and n_q (nq may be NULL). */
+#define RVE_DERIV_FE 0
+#define RVE_DERIV_FOURIER 1
+#define RVE_DERIV_CENTRAL 2
+#define RVE_DERIV_FORWARD 3
+#define RVE_DERIV_LSQ 4
+#define RVE_DERIV_FOURIER2 5
+int rve_set_derivative(rve_t h, int derivative);
+int rve_derivative(rve_t h, int* derivative, int* nq);
+
 /* Measurement hooks (not part of the method).  With timing enabled, every
  * kernel launch of the solver is bracketed by CUDA events on the handle's
  * stream; rve_timing_read returns, per kernel kind, the summed device time in

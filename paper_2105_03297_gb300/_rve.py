@@ -54,6 +54,8 @@ SIGNATURES = {
     "rve_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "rve_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "rve_set_operator_form": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_set_derivative": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_derivative": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rve_operator_form": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "rve_timing_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -235,6 +237,23 @@ class RVE:
         f = C.c_int()
         _check(load().rve_operator_form(self.h, C.byref(f)), "rve_operator_form")
         return {v: k for k, v in self.FORMS.items()}[f.value]
+
+    DERIVATIVES = {"fe": 0, "fourier": 1, "central": 2, "forward": 3, "lsq": 4, "fourier2": 5}
+
+    def set_derivative(self, derivative):
+        """Discrete derivative of the projection: 'fe' (default), 'fourier',
+        'central', 'forward', 'lsq' or 'fourier2' (see include/rve.h).  The
+        non-FE ones need an 'fp64' handle in the 'stress' form."""
+        lib = load()
+        _check(lib.rve_set_derivative(self.h, self.DERIVATIVES[derivative]), "rve_set_derivative")
+        N, m, ns, d = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib.rve_sizes(self.h, C.byref(N), C.byref(m), C.byref(ns), C.byref(d)), "rve_sizes")
+        self.m = m.value
+
+    def derivative(self):
+        d, nq = C.c_int(), C.c_int()
+        _check(load().rve_derivative(self.h, C.byref(d), C.byref(nq)), "rve_derivative")
+        return {v: k for k, v in self.DERIVATIVES.items()}[d.value]
 
     KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other", "force_stencil",
              "strain_update")

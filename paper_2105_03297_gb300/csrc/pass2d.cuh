@@ -18,6 +18,9 @@
 namespace rve {
 
 constexpr double kInvSqrt2 = 0.70710678118654752440;
+}  // namespace rve
+#include "deriv.cuh"
+namespace rve {
 
 // CG scalars: last-block finalisation of <p, C p> (pass A)
 __device__ __forceinline__ void finish_alpha(CgState* cg, double pq) {
@@ -297,10 +300,10 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
 // FFT reads the column straight from the spectrum, the inverse FFT writes it
 // straight back; only the middle transposes and the projection use shared
 // memory.
-template <typename T, int NY, int NT>
+template <typename T, int NY, int NQ, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
-  constexpr int M = 6;
+  constexpr int M = 3 * NQ;   // 6 for the finite elements and two-point Fourier, 3 for one point
   constexpr int LD = FftSplit<NY>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [M][LD]
@@ -326,8 +329,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs
     if (kx == 0 && ky == 0) {
 #pragma unroll
       for (int c = 0; c < M; ++c) s[c] = mkc<T>(0, 0);
-    } else {
+    } else if (NQ == 2 && a.deriv == D_FE) {
       project_2d<T>(s, ex, a.ph[1][ky], a.ih[0], a.ih[1], a.inv_n, a.pmode);
+    } else {
+      const int j[2] = {kx, ky};
+      const C e[2] = {ex, a.ph[1][ky]};
+      C g[2][3];
+      const int nq = deriv_symbols<T, 2>(a.deriv, j, a.n, e, a.ih, g);
+      project_generic<T, 2>(s, g, nq, a.inv_n);
     }
 #pragma unroll
     for (int c = 0; c < M; ++c)
@@ -578,7 +587,7 @@ cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_a_2d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.amode == A_NODAL ? 1 : 2, a.L);
+  dim3 grid(a.n[1] / TY, a.amode == A_NODAL ? 1 : a.nq, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -589,7 +598,7 @@ cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_e_2d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.n[1] / TY, (a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : 2, a.L);
+  dim3 grid(a.n[1] / TY, (a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : a.nq, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -622,9 +631,18 @@ cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
     kn<<<gridn, NTn, smn, s>>>(a);
     return cudaGetLastError();
   }
+  if (a.nq == 1) {
+    constexpr int NT1 = fft_threads<NY, 3>();
+    const size_t sm1 = sizeof(cplx<T>) * 3 * FftSplit<NY>::LD;
+    auto k1 = pass_c_2d<T, NY, 1, NT1>;
+    static bool attr1 = false;
+    if (!attr1) { set_smem_attrs(k1, sm1); attr1 = true; }
+    k1<<<dim3(a.kx, a.L), NT1, sm1, s>>>(a);
+    return cudaGetLastError();
+  }
   constexpr int NT = fft_threads<NY, 6>();
   const size_t sm = sizeof(cplx<T>) * 6 * FftSplit<NY>::LD;
-  auto k = pass_c_2d<T, NY, NT>;
+  auto k = pass_c_2d<T, NY, 2, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
   dim3 grid(a.kx, a.L);

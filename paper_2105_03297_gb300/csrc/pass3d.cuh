@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
   __shared__ double red[NT / 32];
   __shared__ int flag;
   const bool nodal = (a.amode == A_NODAL);
-  const int G = nodal ? 1 : 6;
+  const int G = nodal ? 1 : a.nq;
   const int l = blockIdx.z / G, grp = blockIdx.z % G;
   const int z = blockIdx.y, y0 = blockIdx.x * TY;
   const int ny = a.n[1], nz = a.n[2];
@@ -376,6 +376,56 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d_nodal(Pa
   fft4<T, NZ, R, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
 }
 
+// Pass C for one evaluation point per voxel (the derivatives of Secs. 2.3-2.5,
+// m = 6): P = 6 pencils (k_x, k_y0 + i) of the 6 components per block, so
+// that a block has the 36 transforms of the finite-element pass; row b is
+// component b % 6 of pencil b / 6.  grid (n_x/2+1, ceil(n_y/P), L).
+template <typename T, int NZ, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d_q1(PassArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int P = 6, R = 36;
+  constexpr int LD = FftSplit<NZ>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [R][LD]
+  const int kx = blockIdx.x, ky0 = blockIdx.y * P, l = blockIdx.z;
+  const int ny = a.n[1], KX = a.kx;
+  CgState* cg = a.cg + l;
+  if (!cg->active) return;
+  if (a.cgphase && cg->status != ST_RUN) return;
+  const int64_t stride_c = (int64_t)KX * ny * NZ;
+  C* base = a.spec2 + (int64_t)l * a.m * stride_c + ((int64_t)kx * ny + ky0) * NZ;
+  auto ld_g = [&](int b, int z) -> C {
+    return (ky0 + b / 6 < ny) ? base[(b % 6) * stride_c + (b / 6) * NZ + z] : mkc<T>(0, 0);
+  };
+  auto st_s = [&](int b, int k, C v) { buf[b * LD + k] = v; };
+  fft4<T, NZ, R, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
+  for (int i = threadIdx.x; i < P * NZ; i += NT) {
+    const int pc = i / NZ, kz = i % NZ, ky = ky0 + pc;
+    if (ky >= ny) continue;
+    C sv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sv[c] = buf[(6 * pc + c) * LD + kz];
+    if (kx == 0 && ky == 0 && kz == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sv[c] = mkc<T>(0, 0);
+    } else {
+      const int j[3] = {kx, ky, kz};
+      const C e[3] = {a.ph[0][kx], a.ph[1][ky], a.ph[2][kz]};
+      C g[2][3];
+      const int nq = deriv_symbols<T, 3>(a.deriv, j, a.n, e, a.ih, g);
+      project_generic<T, 3>(sv, g, nq, a.inv_n);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) buf[(6 * pc + c) * LD + kz] = sv[c];
+  }
+  __syncthreads();
+  auto ld_s = [&](int b, int z) -> C { return buf[b * LD + z]; };
+  auto st_g = [&](int b, int k, C v) {
+    if (ky0 + b / 6 < ny) base[(b % 6) * stride_c + (b / 6) * NZ + k] = v;
+  };
+  fft4<T, NZ, R, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
+}
+
 // ---------------------------------------------------------------- pass E
 // grid (n_y/TY, n_z, L*G): G = 6 tetrahedra (6 components each) or one group
 // of the 3 nodal components (E_NODAL); inverse real FFT along x and update.
@@ -391,7 +441,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
   __shared__ double red[NT / 32];
   __shared__ int flag;
   const bool nodal = (a.emode == E_NODAL || a.emode == E_NOUT);
-  const int G = nodal ? 1 : 6;
+  const int G = nodal ? 1 : a.nq;
   const int l = blockIdx.z / G, grp = blockIdx.z % G;
   const int z = blockIdx.y, y0 = blockIdx.x * TY;
   const int ny = a.n[1], nz = a.n[2];
@@ -441,7 +491,7 @@ cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_a_3d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.amode == A_NODAL ? 1 : 6));
+  dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.amode == A_NODAL ? 1 : a.nq));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -452,7 +502,7 @@ cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   auto k = pass_e_3d<T, NX, TY, NT>;
   static bool attr = false;
   if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.n[1] / TY, a.n[2], a.L * ((a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : 6));
+  dim3 grid(a.n[1] / TY, a.n[2], a.L * ((a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : a.nq));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -504,6 +554,15 @@ cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
     if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
     dim3 gridn(a.kx, a.n[1] / P, a.L);
     kn<<<gridn, NTn, smn, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (a.nq == 1) {
+    constexpr int NT1 = fft_threads<NZ, 36>();
+    const size_t sm1 = sizeof(cplx<T>) * 36 * FftSplit<NZ>::LD;
+    auto k1 = pass_c_3d_q1<T, NZ, NT1>;
+    static bool attr1 = false;
+    if (!attr1) { set_smem_attrs(k1, sm1); attr1 = true; }
+    k1<<<dim3(a.kx, (a.n[1] + 5) / 6, a.L), NT1, sm1, s>>>(a);
     return cudaGetLastError();
   }
   constexpr int NT = fft_threads<NZ, 36>();

@@ -80,6 +80,7 @@ struct rve_s {
   int var[2] = {-1, -1};                  // tile variants of passes A and E (-1 = autotune at first solve)
   float tune_ms[2][3] = {{0}};            // measured times of the candidates (last tuning)
   int op_form = RVE_FORM_STRESS;          // order of the operator inside projected CG
+  int deriv = D_FE;                       // discrete derivative of the projection (RVE_DERIV_*)
 };
 
 namespace {
@@ -274,6 +275,7 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   }
   a.lam = (T)h->lam; a.mu2 = (T)h->mu2;
   a.inv_n = (T)(1.0 / (double)h->N);
+  a.deriv = h->deriv;
   a.cg = h->cg; a.part = h->part; a.part_stride = h->part_stride;
   a.var_a = h->var[0] < 0 ? 0 : h->var[0];
   a.var_e = h->var[1] < 0 ? 0 : h->var[1];
@@ -695,6 +697,53 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
   return worst;
 }
 
+// Plain projected CG on the strain fluctuation (the scheme of Sec. 2.1 as the
+// oracle runs it), for derivatives without a finite-element stencil: no nodal
+// state and no real-space residual, FP64 throughout.  r0 = -G C E (pass A
+// broadcasts E), stop on ||r|| <= rel_tol ||r0||; x holds the fluctuation.
+int solve_strain_state(rve_s* h, const double* emac_host, int L, double rel_tol, int max_iter, rve_info* info) {
+  using T = double;
+  CK(cudaMemcpyAsync(h->emac_d, emac_host, (size_t)L * h->ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  std::memset(h->cg_h, 0, (size_t)L * sizeof(CgState));
+  for (int l = 0; l < L; ++l) {
+    h->cg_h[l].active = 1;
+    h->cg_h[l].status = ST_RUN;
+    h->cg_h[l].maxit = max_iter;
+    h->cg_h[l].tol2 = rel_tol * rel_tol;
+  }
+  int rc = write_state(h, L);
+  if (rc) return rc;
+  PassArgs<T> a = pass_args<T>(h, L, h->u, h->emac_d);
+  a.cgphase = 0; a.amode = A_MACRO; a.pmode = P_G; a.emode = E_INIT;
+  CK(apply_passes<T>(h, a));
+  a.cgphase = 1; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
+  {
+    CgRunner<T> runner(h, L, a, 8);
+    std::vector<int> active(L, 1);
+    if ((rc = runner.run(active, (max_iter + 7) / 8 + 1))) return rc;
+  }
+  CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<T>(a, h->stream); }));
+  if ((rc = read_state(h, L))) return rc;
+  int worst = RVE_OK;
+  for (int l = 0; l < L; ++l) {
+    const CgState& c = h->cg_h[l];
+    int st = RVE_OK;
+    if (c.status == ST_BAD) st = RVE_ERR_NONFINITE;
+    else if (c.status != ST_CONV) st = RVE_ERR_NOT_CONVERGED;
+    const double rel = c.rr0 > 0 ? std::sqrt(c.rr / c.rr0) : 0.0;
+    if (info) {
+      info[l].iterations = c.it;
+      info[l].refine_steps = 1;
+      info[l].status = st;
+      info[l].reserved = 0;
+      info[l].rel_residual = rel;
+      info[l].cg_rel_residual = rel;
+    }
+    if (st == RVE_ERR_NONFINITE || (st != RVE_OK && worst == RVE_OK)) worst = st;
+  }
+  return worst;
+}
+
 int compute_mean_stress(rve_s* h, int L) {
   // reuse cg[] slots with active = 1 (homogenise does not read them)
   Fp64Args fa = fp64_args(h, L, h->u, h->emac_d, h->cg);
@@ -707,7 +756,11 @@ int compute_mean_stress(rve_s* h, int L) {
     h->hpart_cap = (int)need;
   }
   int nb = 0;
-  CK(timed(h, K_OTHER, [&] { return launch_homogenise(fa, h->hpart, &nb, h->stream); }));
+  if (h->deriv == D_FE) {
+    CK(timed(h, K_OTHER, [&] { return launch_homogenise(fa, h->hpart, &nb, h->stream); }));
+  } else {
+    CK(timed(h, K_OTHER, [&] { return launch_homogenise_strain(fa, (const double*)h->x, h->hpart, &nb, h->stream); }));
+  }
   std::vector<double> hp(need);
   CK(cudaMemcpyAsync(hp.data(), h->hpart, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -979,7 +1032,9 @@ int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_ite
     rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
     if (rc) return rc;
   }
-  const int st = (h->precision == RVE_MIXED)
+  const int st = (h->deriv != D_FE)
+                     ? solve_strain_state(h, E_macro, L, rel_tol, max_iter, info)
+                     : (h->precision == RVE_MIXED)
                      ? solve_impl<float>(h, E_macro, L, rel_tol, max_iter, info, h->u, h->emac_d)
                      : solve_impl<double>(h, E_macro, L, rel_tol, max_iter, info, h->u, h->emac_d);
   if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED && st != RVE_ERR_NONFINITE) return st;
@@ -1014,6 +1069,7 @@ int rve_effective_tangent(rve_t h, double* C) {
 
 int rve_energy_tangent(rve_t h, double* Ce) {
   if (!h || !Ce || !h->solved) return RVE_ERR_ARG;
+  if (h->deriv != D_FE) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   const int L = h->L_solved;
   const int npair = L * (L + 1) / 2;
@@ -1055,7 +1111,8 @@ int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
     if (rc) return rc;
     dst = tmp;
   }
-  cudaError_t e = launch_strain_field(fa, load_case, dst, h->stream);
+  cudaError_t e = (h->deriv == D_FE) ? launch_strain_field(fa, load_case, dst, h->stream)
+                                      : launch_strain_total(fa, (const double*)h->x, load_case, dst, h->stream);
   if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(eps, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (tmp) cudaFree(tmp);
@@ -1065,6 +1122,7 @@ int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
 int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter, void* grad_E, int ptr_flags) {
   if (!h || !W || !grad_E || !h->solved || h->L_solved != h->ns || !(rel_tol > 0.0) || max_iter < 1)
     return RVE_ERR_ARG;
+  if (h->deriv != D_FE) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   const int ns = h->ns, L = h->L_solved;
   std::vector<double> Minv((size_t)ns * ns), Wp((size_t)ns * L, 0.0);
@@ -1126,6 +1184,7 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
   if (!h || !p || !q) return RVE_ERR_ARG;
   if (apply_material && !h->has_material) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
+  if (int rc = ensure_capacity(h, 1)) return rc;
   const size_t bytes = (size_t)h->m * h->N * h->tsize;
   const cudaMemcpyKind kin = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -1172,6 +1231,7 @@ int rve_set_schedule(rve_t h, const int* variants) {
 
 int rve_set_operator_form(rve_t h, int form) {
   if (!h || (form != RVE_FORM_STRESS && form != RVE_FORM_FACTORED && form != RVE_FORM_NODAL)) return RVE_ERR_ARG;
+  if (form != RVE_FORM_STRESS && h->deriv != D_FE) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   CK(cudaStreamSynchronize(h->stream));
   if (form == RVE_FORM_FACTORED && h->Lcap > 0 && !h->p2) {
@@ -1180,6 +1240,34 @@ int rve_set_operator_form(rve_t h, int form) {
     CK(cudaMemset(h->p2, 0, fld));
   }
   h->op_form = form;
+  return RVE_OK;
+}
+
+int rve_set_derivative(rve_t h, int derivative) {
+  if (!h || derivative < RVE_DERIV_FE || derivative > RVE_DERIV_FOURIER2) return RVE_ERR_ARG;
+  if (derivative != RVE_DERIV_FE && (h->precision != RVE_FP64 || h->op_form != RVE_FORM_STRESS)) return RVE_ERR_ARG;
+  if (derivative == RVE_DERIV_FOURIER2 && h->dim != 2) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
+  CK(cudaStreamSynchronize(h->stream));
+  static_assert((int)RVE_DERIV_FE == (int)D_FE && (int)RVE_DERIV_FOURIER2 == (int)D_FOURIER2, "derivative codes");
+  const int nq = (derivative == RVE_DERIV_FE) ? (h->dim == 2 ? 2 : 6) : (derivative == RVE_DERIV_FOURIER2 ? 2 : 1);
+  if (derivative != h->deriv) {
+    // the field layout depends on n_q: drop the per-load-case buffers and any solution
+    free_L(h);
+    h->solved = false;
+    h->L_solved = 0;
+  }
+  h->deriv = derivative;
+  h->nq = nq;
+  h->m = h->ns * nq;
+  // keep one load case allocated, as after rve_create
+  return ensure_capacity(h, 1);
+}
+
+int rve_derivative(rve_t h, int* derivative, int* nq) {
+  if (!h || !derivative) return RVE_ERR_ARG;
+  *derivative = h->deriv;
+  if (nq) *nq = h->nq;
   return RVE_OK;
 }
 

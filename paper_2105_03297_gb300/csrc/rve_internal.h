@@ -33,6 +33,10 @@ enum ProjMode {
 };
 
 // Everything a pass kernel needs; all pointers are device pointers.
+// discrete derivative (B(k)) of the projection: the linear finite elements or
+// one of the other stencils of Secs. 2.3-2.5 and Appendix C
+enum Deriv { D_FE = 0, D_FOURIER = 1, D_CENTRAL = 2, D_FORWARD = 3, D_LSQ = 4, D_FOURIER2 = 5 };
+
 template <typename T> struct PassArgs {
   int n[3];          // grid sizes (x, y, z); z = 1 in 2D
   int dim, L, m, ns, nq;
@@ -61,6 +65,7 @@ template <typename T> struct PassArgs {
   int cgphase;       // 1 inside the CG loop: passes skip load cases whose CG stopped
   int var_a, var_e;  // tile variants of passes A and E: 0 default rows per block, 1 half, 2 double
   int comp_in;       // number of components in the spectrum for this pass (m or D)
+  int deriv;         // Deriv
 };
 
 // Arguments of the FP64 real-space kernels (residual, homogenisation, adjoint).
@@ -115,6 +120,10 @@ int homogenise_blocks(const Fp64Args& a);
 // part[p * nblk + blk] for the pairs p of (a <= b), a, b < L; returns nblk
 cudaError_t launch_energy(const Fp64Args& a, double* part, int* nblk_out, cudaStream_t s);
 cudaError_t launch_strain_field(const Fp64Args& a, int l, double* out, cudaStream_t s);
+// strain-state solve (FP64 CG vector x [L][m][N] holds the strain fluctuation)
+cudaError_t launch_homogenise_strain(const Fp64Args& a, const double* x, double* part, int* nblk_out,
+                                     cudaStream_t s);
+cudaError_t launch_strain_total(const Fp64Args& a, const double* x, int l, double* out, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const Fp64Args& a, const double* uadj, const double* W, const int* has_adj,
                                 double scale, double* grad, cudaStream_t s);
 
