@@ -301,7 +301,7 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
 // straight back; only the middle transposes and the projection use shared
 // memory.
 template <typename T, int NY, int NQ, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 3 * NQ;   // 6 for the finite elements and two-point Fourier, 3 for one point
   constexpr int LD = FftSplit<NY>::LD;

@@ -83,8 +83,17 @@ __device__ __forceinline__ void fft_reg(C* v) {
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
       C t = o[k];
-      if (k != 0) {
-        const int j = k * (32 / R);
+      const int j = k * (32 / R);
+      if (j == 8) {
+        t = cmul_i<S>(o[k]);  // w = exp(S i pi / 2) = S i
+      } else if (j == 4 || j == 12) {
+        // w = (+-1, S) / sqrt2: one multiplication by 1/sqrt2 per component
+        const T c = (T)kCos32(4);
+        const T sx = (j == 4) ? (T)1 : (T)-1;
+        const T sy = (T)S;
+        t.x = c * (sx * o[k].x - sy * o[k].y);
+        t.y = c * (sx * o[k].y + sy * o[k].x);
+      } else if (k != 0) {
         C w;
         w.x = (T)kCos32(j);
         w.y = (T)(S * kSin32(j));
