@@ -63,6 +63,44 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """Short hash of the CUDA sources and the C header: ties a stored ncu
+    traffic figure to the kernels it was measured on."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2105_03297_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                   + glob.glob(os.path.join(csrc, "*.h"))) + [os.path.join(ROOT, "include", "rve.h")]
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, form, kernel, dim):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.md, or None.
+
+    The table rows are `| workload | form | kernel | bytes per launch | source hash | note |`; a row
+    counts only if its hash is the hash of the kernels being run (otherwise the
+    kernels changed since the counters were taken)."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    name = f"{kernel}_{dim}d"
+    with open(path) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 5 and cells[0] == workload and cells[1] == form and cells[2] == name:
+                try:
+                    return float(cells[3]) if cells[4] == want else None
+                except ValueError:
+                    return None
+    return None
+
+
 def model_bytes(dim, n, s, L_iters, form="stress"):
     """Algorithmic bytes of the CG-iteration passes, per load-case iteration.
 
@@ -464,7 +502,7 @@ def run_gpu(args):
         "cg_iterations_per_solve": cg_iters,
         "c_eff_rel_err_vs_oracle": acc,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": dom,
+                     "frac": achieved / peak, "traffic": measured_traffic(cfg_name, args.form, dom, dim), "kernel": dom,
                      "peak_source": peak_kind},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant"), r.schedule()[0])),
