@@ -119,3 +119,50 @@ def appendix_b_projection(Dsym):
             G[t, :, :, L, :, :] = 0.5 * (np.einsum("il,jm->ijlm", gt, h) + np.einsum("im,jl->ijlm", gt, h)
                                          + np.einsum("jl,im->ijlm", gt, h) + np.einsum("jm,il->ijlm", gt, h))
     return G
+
+
+def laminate_stretch(layer_E, nu, dim, stretch):
+    """Mean first Piola-Kirchhoff stress of a grid-aligned laminate (layers
+    normal to x, equal thickness) under F_macro = diag(stretch, 1, ...), for
+    the St. Venant-Kirchhoff law.
+
+    The exact solution keeps F = diag(f_k, 1, ...) in layer k (a piecewise
+    linear u_x(x), which linear elements represent exactly); equilibrium makes
+    P_xx = E_k M1 f_k (f_k^2 - 1) / 2 the same in every layer and
+    compatibility makes the mean of f_k equal to the stretch (M1 = lambda + 2 mu
+    at unit modulus).  The transverse components are P_yy = P_zz =
+    <E_k lambda1 (f_k^2 - 1) / 2>; the shear components vanish.  Solved by
+    bisection on P_xx with a Newton solve per layer (f_k on the branch
+    f > 1/sqrt3, where P_xx(f) increases).
+    """
+    E = np.asarray(layer_E, dtype=np.float64)
+    lam1, mu1 = lame(1.0, nu)
+    M1 = lam1 + 2.0 * mu1
+
+    def f_of(P):
+        f = np.full_like(E, 1.0)
+        for _ in range(100):
+            g = E * M1 * f * (f * f - 1.0) / 2.0 - P
+            dg = E * M1 * (3.0 * f * f - 1.0) / 2.0
+            f = np.maximum(f - g / dg, 1.0 / np.sqrt(3.0) + 1e-12)
+        return f
+
+    lo, hi = -1.0, 1.0
+    while np.mean(f_of(lo)) > stretch:
+        lo *= 2.0
+    while np.mean(f_of(hi)) < stretch:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.mean(f_of(mid)) < stretch:
+            lo = mid
+        else:
+            hi = mid
+    P = 0.5 * (lo + hi)
+    f = f_of(P)
+    out = np.zeros((dim, dim))
+    out[0, 0] = P
+    for a in range(1, dim):
+        out[a, a] = np.mean(E * lam1 * (f * f - 1.0) / 2.0)
+    return out
+
