@@ -233,6 +233,41 @@ int rve_operator_form(rve_t h, int* form);
 int rve_set_derivative(rve_t h, int derivative);
 int rve_derivative(rve_t h, int* derivative, int* nq);
 
+/* ---- Finite strain ----------------------------------------------------
+ * rve_set_kinematics(h, RVE_FINITE_STRAIN) switches the handle to
+ * deformation gradients: the unknown per element is F = F_macro + H with
+ * F_ia = d chi_i / d r_a (Eq. def-grad), compatibility by the projection of
+ * Eq. original-G built from the element derivatives (G_iabj = delta_ij g_ab,
+ * g from Eq. discrete_projection_op), equilibrium G P(F) = 0 (Eq.
+ * stat-mech-equi-FFT-homogenization) for the first Piola-Kirchhoff stress of
+ * the St. Venant-Kirchhoff law (our reading of the "isotropic finite strain
+ * linear elastic law" of Sec. 3.1): E = (F^T F - I)/2, S = lambda tr(E) I +
+ * 2 mu E, P = F S, with lambda and mu from the voxel's modulus and the
+ * Poisson ratio (plane strain in 2D).  The solve is Newton with each
+ * correction from projected CG on the tangent (G K(F) G is self-adjoint).
+ * Requirements: RVE_FP64, RVE_FORM_STRESS, RVE_DERIV_FE; in 3D n_z <= 128
+ * (RVE_ERR_UNSUPPORTED_SIZE otherwise).  Switching drops the solution and
+ * the per-load-case buffers; rve_solve and rve_adjoint are then refused
+ * (RVE_ERR_ARG), rve_apply_operator applies the bare gradient projection
+ * (apply_material = 0 only) to fields of m = 9 (2D: 2 x 4 + one zero
+ * padding component) or 54 (3D) components, element major, F_ia at
+ * element * D*D + i*D + a.
+ *
+ * rve_solve_finite: F_macro[L][D][D] (row-major F_ia, host), Newton stops when
+ * ||G P(F)|| <= rel_tol ||G P(F_macro)|| or at the round-off level of |P|;
+ * info[l].refine_steps counts Newton steps, .iterations CG iterations,
+ * .rel_residual the final Newton residual, .status RVE_OK /
+ * RVE_ERR_NOT_CONVERGED (max_newton or max_iter reached) / RVE_ERR_NONFINITE.
+ * rve_mean_piola: P[L][D][D], the mean first Piola-Kirchhoff stress.
+ * rve_get_deformation: F[n_q][D][D][N] (FP64) of one load case. */
+#define RVE_SMALL_STRAIN 0
+#define RVE_FINITE_STRAIN 1
+int rve_set_kinematics(rve_t h, int kinematics);
+int rve_solve_finite(rve_t h, const double* F_macro, int L, double rel_tol, int max_newton, int max_iter,
+                     rve_info* info);
+int rve_mean_piola(rve_t h, double* P);
+int rve_get_deformation(rve_t h, int load_case, void* F, int ptr_flags);
+
 /* Measurement hooks (not part of the method).  With timing enabled, every
  * kernel launch of the solver is bracketed by CUDA events on the handle's
  * stream; rve_timing_read returns, per kernel kind, the summed device time in

@@ -55,6 +55,11 @@ SIGNATURES = {
     "rve_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "rve_set_operator_form": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_set_derivative": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_set_kinematics": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_solve_finite": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int, C.c_int,
+                                   C.POINTER(rve_info)]),
+    "rve_mean_piola": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "rve_get_deformation": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "rve_derivative": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rve_operator_form": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "rve_timing_enable": (C.c_int, [C.c_void_p, C.c_int]),
@@ -254,6 +259,39 @@ class RVE:
         d, nq = C.c_int(), C.c_int()
         _check(load().rve_derivative(self.h, C.byref(d), C.byref(nq)), "rve_derivative")
         return {v: k for k, v in self.DERIVATIVES.items()}[d.value]
+
+    def set_kinematics(self, kinematics):
+        """'small' (default) or 'finite' (St. Venant-Kirchhoff deformation
+        gradients; needs an 'fp64' handle, stress form, FE derivative)."""
+        lib = load()
+        _check(lib.rve_set_kinematics(self.h, {"small": 0, "finite": 1}[kinematics]), "rve_set_kinematics")
+        N, m, ns, d = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib.rve_sizes(self.h, C.byref(N), C.byref(m), C.byref(ns), C.byref(d)), "rve_sizes")
+        self.m = m.value
+
+    def solve_finite(self, F_macro, rel_tol=1e-10, max_newton=30, max_iter=20000):
+        """Newton-projected-CG for F_macro[L][D][D]; returns (code, info list)."""
+        D = self.dim
+        Fm = np.ascontiguousarray(np.asarray(F_macro, dtype=np.float64).reshape(-1, D, D))
+        L = Fm.shape[0]
+        self._L = L
+        info = (rve_info * L)()
+        code = load().rve_solve_finite(self.h, Fm.ctypes.data_as(C.POINTER(C.c_double)), L, float(rel_tol),
+                                       int(max_newton), int(max_iter), info)
+        _check(code, "rve_solve_finite", allow=(RVE_ERR_NOT_CONVERGED, RVE_ERR_NONFINITE))
+        return code, [i.as_dict() for i in info]
+
+    def mean_piola(self):
+        P = np.zeros((self._L, self.dim, self.dim))
+        _check(load().rve_mean_piola(self.h, P.ctypes.data_as(C.POINTER(C.c_double))), "rve_mean_piola")
+        return P
+
+    def get_deformation(self, load_case):
+        nq = 2 if self.dim == 2 else 6
+        out = np.zeros((nq, self.dim, self.dim, self.N))
+        p, flag, _k = _dptr(out)
+        _check(load().rve_get_deformation(self.h, int(load_case), p, flag), "rve_get_deformation")
+        return out
 
     KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other", "force_stencil",
              "strain_update")

@@ -20,6 +20,7 @@ namespace rve {
 constexpr double kInvSqrt2 = 0.70710678118654752440;
 }  // namespace rve
 #include "deriv.cuh"
+#include "finite.cuh"
 namespace rve {
 
 // CG scalars: last-block finalisation of <p, C p> (pass A)
@@ -303,7 +304,8 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
 template <typename T, int NY, int NQ, int NT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
-  constexpr int M = 3 * NQ;   // 6 for the finite elements and two-point Fourier, 3 for one point
+  constexpr int M = 3 * NQ;   // 6 for the finite elements and two-point Fourier, 3 for one point,
+                              // 9 for finite-strain gradients (8 + padding)
   constexpr int LD = FftSplit<NY>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [M][LD]
@@ -326,7 +328,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_c_2d(PassArgs
     C s[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) s[c] = (c < cin) ? buf[c * LD + ky] : mkc<T>(0, 0);
-    if (kx == 0 && ky == 0) {
+    if constexpr (NQ == 3) {
+      // finite strain: deformation gradients of the two triangles (+ padding)
+      const C e2[2] = {ex, a.ph[1][ky]};
+      C g[6][3];
+      fe_gradients<T, 2>(e2, a.ih, g);
+      auto col = [&](int c) -> C& { return s[c]; };
+      project_finite<T, 2, 2>(col, g, a.inv_n, kx == 0 && ky == 0);
+    } else if (kx == 0 && ky == 0) {
 #pragma unroll
       for (int c = 0; c < M; ++c) s[c] = mkc<T>(0, 0);
     } else if (NQ == 2 && a.deriv == D_FE) {
@@ -629,6 +638,15 @@ cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
     if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
     dim3 gridn((a.kx + P - 1) / P, a.L);
     kn<<<gridn, NTn, smn, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (a.nq == 3) {
+    constexpr int NT3 = fft_threads<NY, 9>();
+    const size_t sm3 = sizeof(cplx<T>) * 9 * FftSplit<NY>::LD;
+    auto k3 = pass_c_2d<T, NY, 3, NT3>;
+    static bool attr3 = false;
+    if (!attr3) { set_smem_attrs(k3, sm3); attr3 = true; }
+    k3<<<dim3(a.kx, a.L), NT3, sm3, s>>>(a);
     return cudaGetLastError();
   }
   if (a.nq == 1) {

@@ -426,6 +426,39 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d_q1(PassA
   fft4<T, NZ, R, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
 }
 
+// Pass C for finite strain (P_FINITE): one (k_x, k_y) pencil of the 54
+// deformation-gradient components (6 tetrahedra x 3 x 3) per block.
+// grid (n_x/2+1, n_y, L).
+template <typename T, int NZ, int NT>
+__global__ void __launch_bounds__(NT, 1) pass_c_3d_fs(PassArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int R = 54;
+  constexpr int LD = FftSplit<NZ>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [R][LD]
+  const int kx = blockIdx.x, ky = blockIdx.y, l = blockIdx.z;
+  const int ny = a.n[1], KX = a.kx;
+  CgState* cg = a.cg + l;
+  if (!cg->active) return;
+  if (a.cgphase && cg->status != ST_RUN) return;
+  const int64_t stride_c = (int64_t)KX * ny * NZ;
+  C* pen = a.spec2 + (int64_t)l * a.m * stride_c + ((int64_t)kx * ny + ky) * NZ;
+  auto ld_g = [&](int c, int z) -> C { return pen[c * stride_c + z]; };
+  auto st_s = [&](int c, int k, C v) { buf[c * LD + k] = v; };
+  fft4<T, NZ, R, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
+  for (int kz = threadIdx.x; kz < NZ; kz += NT) {
+    const C e[3] = {a.ph[0][kx], a.ph[1][ky], a.ph[2][kz]};
+    C g[6][3];
+    fe_gradients<T, 3>(e, a.ih, g);
+    auto col = [&](int c) -> C& { return buf[c * LD + kz]; };
+    project_finite<T, 3, 6>(col, g, a.inv_n, kx == 0 && ky == 0 && kz == 0);
+  }
+  __syncthreads();
+  auto ld_s = [&](int c, int z) -> C { return buf[c * LD + z]; };
+  auto st_g = [&](int c, int k, C v) { pen[c * stride_c + k] = v; };
+  fft4<T, NZ, R, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
+}
+
 // ---------------------------------------------------------------- pass E
 // grid (n_y/TY, n_z, L*G): G = 6 tetrahedra (6 components each) or one group
 // of the 3 nodal components (E_NODAL); inverse real FFT along x and update.
@@ -554,6 +587,16 @@ cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
     if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
     dim3 gridn(a.kx, a.n[1] / P, a.L);
     kn<<<gridn, NTn, smn, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (a.pmode == P_FINITE) {
+    constexpr int NTf = fft_threads<NZ, 54>();
+    const size_t smf = sizeof(cplx<T>) * 54 * FftSplit<NZ>::LD;
+    if (smf > 227 * 1024) return cudaErrorInvalidConfiguration;   // FP64 at n_z = 256
+    auto kf = pass_c_3d_fs<T, NZ, NTf>;
+    static bool attrf = false;
+    if (!attrf) { set_smem_attrs(kf, smf); attrf = true; }
+    kf<<<dim3(a.kx, a.n[1], a.L), NTf, smf, s>>>(a);
     return cudaGetLastError();
   }
   if (a.nq == 1) {

@@ -19,6 +19,7 @@
 #include <memory>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <new>
 #include <thread>
 #include <vector>
@@ -81,6 +82,10 @@ struct rve_s {
   float tune_ms[2][3] = {{0}};            // measured times of the candidates (last tuning)
   int op_form = RVE_FORM_STRESS;          // order of the operator inside projected CG
   int deriv = D_FE;                       // discrete derivative of the projection (RVE_DERIV_*)
+  int finite = 0;                         // RVE_FINITE_STRAIN: fields are deformation gradients
+  double* Fs = nullptr;                   // [Lcap][m][N] deformation gradient (finite strain)
+  double* fmac_d = nullptr;               // [64][D*D] macroscopic deformation gradients
+  std::vector<double> P_h;                // [L][D*D] mean first Piola-Kirchhoff stress
 };
 
 namespace {
@@ -192,6 +197,7 @@ int64_t spec_elems(const rve_s* h) {
 
 void free_L(rve_s* h) {
   free_dev(h->x); free_dev(h->r); free_dev(h->p); free_dev(h->p2); free_dev(h->fbuf);
+  free_devp(h->Fs); free_devp(h->fmac_d);
   free_dev(h->spec); free_dev(h->spec2);
   free_devp(h->u); free_devp(h->uadj); free_devp(h->part); free_devp(h->cg);
   free_devp(h->emac_d); free_devp(h->emac_adj_d);
@@ -258,7 +264,10 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   PassArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   for (int i = 0; i < 3; ++i) a.n[i] = h->n[i];
-  a.dim = h->dim; a.L = L; a.m = h->m; a.ns = h->ns; a.nq = h->nq;
+  a.dim = h->dim; a.L = L; a.m = h->m; a.ns = h->ns;
+  // passes A and E work in groups of n_s components: n_q groups for strain
+  // fields, m / n_s for finite-strain gradient fields
+  a.nq = h->finite ? h->m / h->ns : h->nq;
   a.N = h->N; a.kx = h->kx;
   a.E = (const T*)h->Ein;
   a.lcs = h->lcs > 0 ? h->lcs : L;
@@ -378,7 +387,24 @@ template <typename T> cudaError_t apply_nodal(rve_s* h, const PassArgs<T>& a, in
 // The k-th CG iteration of a batch (k counts from 0 at the start of an inner
 // solve; batches hold an even number of iterations, so k's parity is the
 // parity of the CG iteration count of every slot still running).
+// One Newton-CG iteration of the finite-strain solve: direction update and
+// tangent t = K(F) : p (with <p, t>), then G t by the FFT passes with the
+// r update of pass E.
+inline cudaError_t apply_finite(rve_s* h, const PassArgs<double>& a) {
+  cudaError_t e = timed(h, K_FS, [&] { return launch_fs_dir_tangent(a, h->Fs, (double*)h->fbuf, h->stream); });
+  PassArgs<double> b = a;
+  b.amode = A_BARE; b.pmode = P_FINITE; b.emode = E_CG;
+  b.in = (const double*)h->fbuf;
+  if (e == cudaSuccess) e = pass_a<double>(h, b);
+  if (e == cudaSuccess) e = pass_mid<double>(h, b);
+  if (e == cudaSuccess) e = pass_e<double>(h, b);
+  return e;
+}
+
 template <typename T> cudaError_t cg_iteration(rve_s* h, const PassArgs<T>& a, int k) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->finite) return apply_finite(h, a);
+  }
   if (h->op_form == RVE_FORM_FACTORED) return apply_factored<T>(h, a, k & 1);
   if (h->op_form == RVE_FORM_NODAL) return apply_nodal<T>(h, a, k & 1);
   return apply_passes<T>(h, a);
@@ -744,6 +770,118 @@ int solve_strain_state(rve_s* h, const double* emac_host, int L, double rel_tol,
   return worst;
 }
 
+// Finite strain (St. Venant-Kirchhoff), FP64: Newton on G P(F) = 0 with each
+// correction from projected CG on G K(F) dH = -G P(F) (Eq.
+// stat-mech-equi-FFT-homogenization with the gradient projection of Eq.
+// original-G).  Newton stops when ||G P(F)|| <= rel_tol ||G P(F_macro)|| or
+// at the round-off level of |P|; the CG of step k stops at a relative
+// residual of max(min(1e-2, frel_k), 0.1 rel_tol / frel_k), capped at 0.5.
+int solve_finite(rve_s* h, const double* Fmac_host, int L, double rel_tol, int max_newton, int max_iter,
+                 rve_info* info) {
+  const int D = h->dim, DD = D * D;
+  if (!h->Fs && dev_alloc((void**)&h->Fs, (size_t)h->Lcap * h->m * h->N * sizeof(double))) return RVE_ERR_OOM;
+  if (!h->fmac_d && dev_alloc((void**)&h->fmac_d, (size_t)64 * 9 * sizeof(double))) return RVE_ERR_OOM;
+  CK(cudaMemcpyAsync(h->fmac_d, Fmac_host, (size_t)L * DD * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  std::memset(h->cg_h, 0, (size_t)L * sizeof(CgState));
+  for (int l = 0; l < L; ++l) { h->cg_h[l].active = 1; h->cg_h[l].status = ST_RUN; }
+  int rc = write_state(h, L);
+  if (rc) return rc;
+  PassArgs<double> a = pass_args<double>(h, L, h->u, h->emac_d);
+  CK(timed(h, K_OTHER, [&] { return launch_fs_init(a, h->Fs, h->fmac_d, h->stream); }));
+  std::vector<double> r0(L, 0.0), frel(L, 1.0), cgrel(L, 0.0);
+  std::vector<int> iters(L, 0), steps(L, 0), active(L, 1), bad(L, 0), done(L, 0);
+  std::unique_ptr<CgRunner<double>> runner;
+  for (int newton = 0;; ++newton) {
+    // residual r = -G P(F) (pass E in init mode also zeroes x and sets rr0)
+    a.cgphase = 0;
+    CK(timed(h, K_RES, [&] { return launch_fs_stress(a, h->Fs, (double*)h->fbuf, h->stream); }));
+    PassArgs<double> b = a;
+    b.amode = A_BARE; b.pmode = P_FINITE; b.emode = E_INIT;
+    b.in = (const double*)h->fbuf;
+    CK(apply_passes<double>(h, b));
+    if ((rc = read_state(h, L))) return rc;
+    bool any = false;
+    for (int l = 0; l < L; ++l) {
+      if (!active[l]) continue;
+      const double rn = std::sqrt(h->cg_h[l].rr0);
+      if (!std::isfinite(rn)) { bad[l] = 1; active[l] = 0; continue; }
+      if (newton == 0) r0[l] = rn;
+      frel[l] = r0[l] > 0.0 ? rn / r0[l] : 0.0;
+      const bool at_floor = rn <= 1e-13 * std::sqrt(h->cg_h[l].fa2);
+      if (at_floor || frel[l] <= rel_tol) { done[l] = 1; active[l] = 0; continue; }
+      if (newton >= max_newton || iters[l] >= max_iter) { active[l] = 0; continue; }
+      any = true;
+    }
+    if (!any) break;
+    for (int l = 0; l < L; ++l) {
+      double tau = std::fmax(std::fmin(1e-2, frel[l]), 0.1 * rel_tol / std::fmax(frel[l], 1e-300));
+      tau = std::fmin(tau, 0.5);
+      h->cg_h[l].active = active[l];
+      h->cg_h[l].status = ST_RUN;
+      h->cg_h[l].it = 0;
+      h->cg_h[l].maxit = max_iter - iters[l];
+      h->cg_h[l].tol2 = tau * tau;
+      h->cg_h[l].cnt_a = h->cg_h[l].cnt_e = h->cg_h[l].cnt_r = 0;
+    }
+    if ((rc = write_state(h, L))) return rc;
+    a.cgphase = 1; a.amode = A_BARE; a.pmode = P_FINITE; a.emode = E_CG;
+    if (!runner) runner.reset(new CgRunner<double>(h, L, a, 8));
+    if ((rc = runner->run(active, (max_iter + 7) / 8 + 1))) return rc;
+    CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<double>(a, h->stream); }));
+    if ((rc = read_state(h, L))) return rc;
+    for (int l = 0; l < L; ++l) {
+      if (!active[l]) continue;
+      iters[l] += h->cg_h[l].it;
+      steps[l] += 1;
+      cgrel[l] = h->cg_h[l].rr0 > 0 ? std::sqrt(h->cg_h[l].rr / h->cg_h[l].rr0) : 0.0;
+      if (h->cg_h[l].status == ST_BAD) bad[l] = 1;
+    }
+    CK(timed(h, K_OTHER, [&] { return launch_fs_add(a, h->Fs, h->stream); }));
+    for (int l = 0; l < L; ++l)
+      if (bad[l]) { active[l] = 0; h->cg_h[l].active = 0; }
+    for (int l = 0; l < L; ++l) h->cg_h[l].active = active[l];
+    if ((rc = write_state(h, L))) return rc;
+  }
+  // mean first Piola-Kirchhoff stress over all elements
+  for (int l = 0; l < L; ++l) h->cg_h[l].active = 1;
+  if ((rc = write_state(h, L))) return rc;
+  const int nb = fs_mean_blocks(a);
+  const size_t need = (size_t)L * DD * nb;
+  if ((int)need > h->hpart_cap) {
+    free_devp(h->hpart);
+    if ((rc = dev_alloc((void**)&h->hpart, need * sizeof(double)))) return rc;
+    h->hpart_cap = (int)need;
+  }
+  CK(timed(h, K_OTHER, [&] { return launch_fs_mean(a, h->Fs, h->hpart, h->stream); }));
+  std::vector<double> hp(need);
+  CK(cudaMemcpyAsync(hp.data(), h->hpart, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) flush_timing(h);
+  h->P_h.assign((size_t)L * DD, 0.0);
+  const double scale = 1.0 / ((double)h->N * (D == 2 ? 2 : 6));
+  for (int l = 0; l < L; ++l)
+    for (int c = 0; c < DD; ++c) {
+      double t = 0.0;
+      const double* src = hp.data() + ((size_t)l * DD + c) * nb;
+      for (int q = 0; q < nb; ++q) t += src[q];
+      h->P_h[(size_t)l * DD + c] = t * scale;
+    }
+  int worst = RVE_OK;
+  for (int l = 0; l < L; ++l) {
+    int st = bad[l] ? RVE_ERR_NONFINITE : (done[l] ? RVE_OK : RVE_ERR_NOT_CONVERGED);
+    if (info) {
+      info[l].iterations = iters[l];
+      info[l].refine_steps = steps[l];
+      info[l].status = st;
+      info[l].reserved = 0;
+      info[l].rel_residual = frel[l];
+      info[l].cg_rel_residual = cgrel[l];
+    }
+    if (st == RVE_ERR_NONFINITE || (st != RVE_OK && worst == RVE_OK)) worst = st;
+  }
+  return worst;
+}
+
 int compute_mean_stress(rve_s* h, int L) {
   // reuse cg[] slots with active = 1 (homogenise does not read them)
   Fp64Args fa = fp64_args(h, L, h->u, h->emac_d, h->cg);
@@ -1022,7 +1160,7 @@ int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_fla
 
 int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info) {
   if (!h || !E_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_iter < 1) return RVE_ERR_ARG;
-  if (!h->has_material) return RVE_ERR_ARG;
+  if (!h->has_material || h->finite) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   for (int i = 0; i < L * h->ns; ++i) if (!std::isfinite(E_macro[i])) return RVE_ERR_ARG;
   h->solved = false;
@@ -1194,6 +1332,7 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
   int rc = write_state(h, 1);
   if (rc) return rc;
   h->solved = false;  // the operator shares the solve's buffers
+  if (h->finite && apply_material) return RVE_ERR_ARG;
   if (h->tsize == 4) {
     PassArgs<float> a = pass_args<float>(h, 1, h->u, h->emac_d);
     a.amode = apply_material ? A_FIELD : A_BARE; a.pmode = P_G; a.emode = E_OUT;
@@ -1201,7 +1340,7 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
     CK(apply_passes<float>(h, a));
   } else {
     PassArgs<double> a = pass_args<double>(h, 1, h->u, h->emac_d);
-    a.amode = apply_material ? A_FIELD : A_BARE; a.pmode = P_G; a.emode = E_OUT;
+    a.amode = apply_material ? A_FIELD : A_BARE; a.pmode = h->finite ? P_FINITE : P_G; a.emode = E_OUT;
     a.in = (const double*)h->fbuf; a.out = (double*)h->x;
     CK(apply_passes<double>(h, a));
   }
@@ -1231,7 +1370,7 @@ int rve_set_schedule(rve_t h, const int* variants) {
 
 int rve_set_operator_form(rve_t h, int form) {
   if (!h || (form != RVE_FORM_STRESS && form != RVE_FORM_FACTORED && form != RVE_FORM_NODAL)) return RVE_ERR_ARG;
-  if (form != RVE_FORM_STRESS && h->deriv != D_FE) return RVE_ERR_ARG;
+  if (form != RVE_FORM_STRESS && (h->deriv != D_FE || h->finite)) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   CK(cudaStreamSynchronize(h->stream));
   if (form == RVE_FORM_FACTORED && h->Lcap > 0 && !h->p2) {
@@ -1247,6 +1386,7 @@ int rve_set_derivative(rve_t h, int derivative) {
   if (!h || derivative < RVE_DERIV_FE || derivative > RVE_DERIV_FOURIER2) return RVE_ERR_ARG;
   if (derivative != RVE_DERIV_FE && (h->precision != RVE_FP64 || h->op_form != RVE_FORM_STRESS)) return RVE_ERR_ARG;
   if (derivative == RVE_DERIV_FOURIER2 && h->dim != 2) return RVE_ERR_ARG;
+  if (h->finite) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   CK(cudaStreamSynchronize(h->stream));
   static_assert((int)RVE_DERIV_FE == (int)D_FE && (int)RVE_DERIV_FOURIER2 == (int)D_FOURIER2, "derivative codes");
@@ -1268,6 +1408,60 @@ int rve_derivative(rve_t h, int* derivative, int* nq) {
   if (!h || !derivative) return RVE_ERR_ARG;
   *derivative = h->deriv;
   if (nq) *nq = h->nq;
+  return RVE_OK;
+}
+
+int rve_set_kinematics(rve_t h, int kinematics) {
+  if (!h || (kinematics != RVE_SMALL_STRAIN && kinematics != RVE_FINITE_STRAIN)) return RVE_ERR_ARG;
+  const bool fin = kinematics == RVE_FINITE_STRAIN;
+  if (fin && (h->precision != RVE_FP64 || h->op_form != RVE_FORM_STRESS || h->deriv != D_FE)) return RVE_ERR_ARG;
+  if (fin && h->dim == 3 && h->n[2] > 128) return RVE_ERR_UNSUPPORTED_SIZE;   // 54 pencil rows in shared memory
+  if (int jr = join_user(h)) return jr;
+  CK(cudaStreamSynchronize(h->stream));
+  if ((int)fin != h->finite) {
+    free_L(h);
+    h->solved = false;
+    h->L_solved = 0;
+  }
+  h->finite = fin ? 1 : 0;
+  h->m = fin ? (h->dim == 2 ? 9 : 54) : h->ns * h->nq;
+  if (h->var[0] < 0) h->var[0] = 0;
+  if (h->var[1] < 0) h->var[1] = 0;
+  return ensure_capacity(h, 1);
+}
+
+int rve_solve_finite(rve_t h, const double* F_macro, int L, double rel_tol, int max_newton, int max_iter,
+                     rve_info* info) {
+  if (!h || !F_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_newton < 0 || max_iter < 1) return RVE_ERR_ARG;
+  if (!h->has_material || !h->finite) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
+  for (int i = 0; i < L * h->dim * h->dim; ++i) if (!std::isfinite(F_macro[i])) return RVE_ERR_ARG;
+  h->solved = false;
+  const int Lold = h->Lcap;
+  int rc = ensure_capacity(h, L);
+  if (rc) return rc;
+  if (h->Lcap != Lold) free_devp(h->Fs);   // buffers were regrown
+  const int st = solve_finite(h, F_macro, L, rel_tol, max_newton, max_iter, info);
+  if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED && st != RVE_ERR_NONFINITE) return st;
+  h->L_solved = L;
+  h->solved = true;
+  return st;
+}
+
+int rve_mean_piola(rve_t h, double* P) {
+  if (!h || !P || !h->solved || !h->finite) return RVE_ERR_ARG;
+  std::memcpy(P, h->P_h.data(), h->P_h.size() * sizeof(double));
+  return RVE_OK;
+}
+
+int rve_get_deformation(rve_t h, int load_case, void* F, int ptr_flags) {
+  if (!h || !F || !h->solved || !h->finite || load_case < 0 || load_case >= h->L_solved) return RVE_ERR_ARG;
+  if (int jr = join_user(h)) return jr;
+  const int nq = h->dim == 2 ? 2 : 6;
+  const size_t bytes = (size_t)nq * h->dim * h->dim * h->N * sizeof(double);
+  const cudaMemcpyKind k = (ptr_flags & RVE_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(F, h->Fs + (size_t)load_case * h->m * h->N, bytes, k, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return RVE_OK;
 }
 

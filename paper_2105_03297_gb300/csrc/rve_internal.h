@@ -29,7 +29,8 @@ enum ProjMode {
   P_G = 0,       // eps^ = B (B^H B)^-1 B^H sigma^  (m -> m)
   P_NODAL_IN = 1,  // eps^ = B (B^H B)^-1 f^          (D -> m)
   P_NODAL_OUT = 2, // u^ = (B^H B)^-1 B^H eps^        (m -> D)
-  P_SOLVE = 3      // w^ = (B^H B)^-1 f^              (D -> D, factored form)
+  P_SOLVE = 3,     // w^ = (B^H B)^-1 f^              (D -> D, factored form)
+  P_FINITE = 4     // H^ = G H^ on deformation gradients (finite strain, n_q D^2 components)
 };
 
 // Everything a pass kernel needs; all pointers are device pointers.
@@ -120,6 +121,13 @@ int homogenise_blocks(const Fp64Args& a);
 // part[p * nblk + blk] for the pairs p of (a <= b), a, b < L; returns nblk
 cudaError_t launch_energy(const Fp64Args& a, double* part, int* nblk_out, cudaStream_t s);
 cudaError_t launch_strain_field(const Fp64Args& a, int l, double* out, cudaStream_t s);
+// finite strain (FP64): F, P, t are [L][m][N] deformation-gradient fields
+cudaError_t launch_fs_init(const PassArgs<double>& a, double* F, const double* Fmac, cudaStream_t s);
+cudaError_t launch_fs_stress(const PassArgs<double>& a, const double* F, double* P, cudaStream_t s);
+cudaError_t launch_fs_dir_tangent(const PassArgs<double>& a, const double* F, double* t, cudaStream_t s);
+cudaError_t launch_fs_add(const PassArgs<double>& a, double* F, cudaStream_t s);
+int fs_mean_blocks(const PassArgs<double>& a);
+cudaError_t launch_fs_mean(const PassArgs<double>& a, const double* F, double* part, cudaStream_t s);
 // strain-state solve (FP64 CG vector x [L][m][N] holds the strain fluctuation)
 cudaError_t launch_homogenise_strain(const Fp64Args& a, const double* x, double* part, int* nblk_out,
                                      cudaStream_t s);
