@@ -259,6 +259,8 @@ def run_reference(args):
     if rank != 0:
         return
     cfg_name, prec, tol = WORKLOADS[args.workload]
+    import microstructures as ms
+    cfg = ms.config_inputs(cfg_name)
     its_gold, _ = golden_iterations(cfg_name)
     total_its = sum(its_gold) if its_gold else None
     per_step = []
@@ -277,7 +279,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3 if solve_s else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg_name},
+        "config": {"workload": cfg_name, "grid": list(cfg["n"]), "load_cases": len(cfg["E_macro"]),
+                   "precision": "fp64 (CPU oracle)", "rel_tol": tol, "parallelism": "one CPU thread"},
         "ms_per_cg_iteration": ms_it,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sample_its} FP64 CG iterations of one load case of {cfg_name} "
