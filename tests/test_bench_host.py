@@ -1,0 +1,38 @@
+"""Host logic of bench.py (CPU): the byte models and the stored-traffic lookup."""
+import os
+
+import numpy as np
+
+import bench
+
+
+def test_byte_models():
+    n, s = (1024, 1024), 4
+    N = n[0] * n[1]
+    spec = 6 * (n[0] // 2 + 1) * n[1] * 2 * s
+    mb = bench.model_bytes(2, n, s, 1)
+    assert mb["pass_a"] == 5 * 6 * N * s + N * s + spec
+    assert mb["pass_c"] == 2 * spec and mb["pass_e"] == spec + 2 * 6 * N * s
+    mb3 = bench.model_bytes(3, (64, 64, 64), 8, 1)
+    assert set(mb3) == {"pass_a", "pass_b", "pass_c", "pass_d", "pass_e"}
+    nod = bench.model_bytes(3, (64, 64, 64), 4, 1, "nodal")
+    assert nod["force_stencil"] == (6 * 3 + 1) * 64 ** 3 * 4
+    # the nodal form moves far fewer bytes than the stress form
+    assert sum(nod.values()) < 0.2 * sum(bench.model_bytes(3, (64, 64, 64), 4, 1).values())
+
+
+def test_traffic_rows_follow_the_kernel_hash():
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and all(c in "0123456789abcdef" for c in h)
+    path = os.path.join(bench.ROOT, "profiles", "traffic.md")
+    rows = [[c.strip() for c in line.strip().strip("|").split("|")] for line in open(path)
+            if line.startswith("| ") and not line.startswith("| workload")]
+    assert rows
+    for w, form, kernel, b, hh, _note in rows:
+        kind, dim = kernel.rsplit("_", 1)
+        got = bench.measured_traffic(w, form, kind, int(dim[0]))
+        if hh == h:
+            assert np.isclose(got, float(b))
+        else:
+            assert got is None
+    assert bench.measured_traffic("gauss1024", "stress", "no_such_pass", 2) is None
