@@ -64,14 +64,14 @@ def peaks():
 
 
 def kernel_source_hash():
-    """Short hash of the CUDA sources and the C header: ties a stored ncu
-    traffic figure to the kernels it was measured on."""
+    """Short hash of the CUDA sources (csrc/): ties a stored ncu traffic
+    figure to the kernels it was measured on."""
     import glob
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2105_03297_gb300", "csrc")
     files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
-                   + glob.glob(os.path.join(csrc, "*.h"))) + [os.path.join(ROOT, "include", "rve.h")]
+                   + glob.glob(os.path.join(csrc, "*.h")))
     for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:

@@ -277,8 +277,11 @@ int rve_get_deformation(rve_t h, int load_case, void* F, int ptr_flags);
  * 1 pass B (y FFT, 3D), 2 pass C (last-axis FFT + projection or nodal solve),
  * 3 pass D (inverse y FFT, 3D), 4 pass E (inverse x FFT + CG update; factored
  * form: inverse x FFT of w); 5 the FP64 residual; 6 every other launch
- * (right-hand side, displacement recovery, homogenisation); 7 the force
- * stencil and 8 the strain update of the factored form. */
+ * (right-hand side, displacement recovery, homogenisation); 7 the real-space
+ * material kernel of the factored and nodal forms (force stencil / force
+ * kernel) and of finite strain (direction update and tangent); 8 the
+ * real-space update kernel of the factored and nodal forms.  Kind 5 also
+ * counts the finite-strain stress evaluations of the Newton residual. */
 #define RVE_NKINDS 9
 int rve_timing_enable(rve_t h, int enable);
 int rve_timing_read(rve_t h, double* ms /*[RVE_NKINDS]*/, int64_t* launches /*[RVE_NKINDS]*/);

@@ -293,6 +293,8 @@ class RVE:
         _check(load().rve_get_deformation(self.h, int(load_case), p, flag), "rve_get_deformation")
         return out
 
+    # kind 7: real-space material kernel of the factored / nodal forms and of
+    # finite strain; kind 8: real-space update kernel of the factored / nodal forms
     KINDS = ("pass_a", "pass_b", "pass_c", "pass_d", "pass_e", "residual", "other", "force_stencil",
              "strain_update")
 
