@@ -199,3 +199,95 @@ def dense_minimiser(n, E, nu, Emac, length=None):
     f = fem.load_vector(Emac)
     u = np.linalg.pinv(K, rcond=1e-12) @ f
     return fem.element_strains(Emac, u)
+
+
+def finite_strain_fem(n, E, nu, Fmac, length=None, tol=1e-13, max_newton=50):
+    """Periodic finite-strain linear-FE problem in real space (dense; tiny grids).
+
+    The same St. Venant-Kirchhoff law as ``finite_strain`` but no Fourier
+    symbols and no projection: nodal displacement fluctuations u (D per node),
+    F_e = F_macro + sum_v u_v (x) grad N_v on every simplex, and Newton on the
+    stationarity of sum_e |e| W(F_e), W = lambda/2 tr(E)^2 + mu E : E, with the
+    consistent tangent assembled densely; the constant null space is removed
+    by a least-squares solve.  Returns (F per element [n_q, D, D, N], mean
+    first Piola-Kirchhoff stress [D, D], Newton steps).
+    """
+    n = tuple(int(v) for v in n)
+    D = len(n)
+    Ev = np.asarray(E, dtype=np.float64).reshape(-1)
+    N = Ev.size
+    lam1 = nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu1 = 1.0 / (2.0 * (1.0 + nu))
+    h = np.array(voxel_size(n, length))
+    idx = np.array(np.unravel_index(np.arange(N), array_shape(n))[::-1]).T
+    strides = np.array([int(np.prod(n[:a])) for a in range(D)])
+    elems = []
+    for verts in element_vertices(D):
+        grads, vol = shape_function_gradients(verts * h)
+        nodes = np.stack([((idx + v[None, :]) % np.array(n)[None, :]) @ strides for v in verts], axis=1)
+        elems.append((grads, vol, nodes))
+    Fm = np.asarray(Fmac, dtype=np.float64).reshape(D, D)
+    ndof = N * D
+    I = np.eye(D)
+
+    def element_F(u):
+        out = []
+        for grads, vol, nodes in elems:
+            U = u.reshape(N, D)[nodes]                           # (N, D+1, D): u_v,i
+            H = np.einsum("evi,va->eia", U, grads)
+            out.append(Fm[None] + H)
+        return out
+
+    def pk(F, e):
+        C = np.einsum("eki,ekj->eij", F, F)
+        Eg = 0.5 * (C - I[None])
+        tr = np.trace(Eg, axis1=1, axis2=2)
+        S = e[:, None, None] * (lam1 * tr[:, None, None] * I[None] + 2.0 * mu1 * Eg)
+        return S
+
+    def assemble(u):
+        g = np.zeros(ndof)
+        K = np.zeros((ndof, ndof))
+        for (grads, vol, nodes), F in zip(elems, element_F(u)):
+            S = pk(F, Ev)
+            P = np.einsum("eik,ekj->eij", F, S)
+            # internal force on dof (v, i): sum_a P_ia dN_v/dx_a
+            fe = vol * np.einsum("eia,va->evi", P, grads)
+            dofs = (nodes[:, :, None] * D + np.arange(D)[None, None, :])   # (N, D+1, D)
+            np.add.at(g, dofs.reshape(-1), fe.reshape(-1))
+            # tangent dP/dF contracted with the shape-function gradients
+            A = np.zeros((N, D, D, D, D))
+            for j in range(D):
+                for b in range(D):
+                    dF = np.zeros((N, D, D))
+                    dF[:, j, b] = 1.0
+                    FtdF = np.einsum("eki,ekj->eij", F, dF)
+                    dE = 0.5 * (FtdF + np.swapaxes(FtdF, 1, 2))
+                    dtr = np.trace(dE, axis1=1, axis2=2)
+                    dS = Ev[:, None, None] * (lam1 * dtr[:, None, None] * I[None] + 2.0 * mu1 * dE)
+                    A[:, :, :, j, b] = np.einsum("eik,ekj->eij", dF, S) + np.einsum("eik,ekj->eij", F, dS)
+            Ke = vol * np.einsum("ua,eiajb,vb->euivj", grads, A, grads)           # (N, D+1, D, D+1, D)
+            d = dofs.reshape(N, -1)
+            m = d.shape[1]
+            np.add.at(K, (np.repeat(d, m, axis=1).reshape(-1), np.tile(d, (1, m)).reshape(-1)),
+                      Ke.reshape(N, m * m).reshape(-1))
+        return g, K
+
+    u = np.zeros(ndof)
+    g0 = None
+    steps = 0
+    while steps < max_newton:
+        g, K = assemble(u)
+        gn = np.linalg.norm(g)
+        if g0 is None:
+            g0 = gn
+        if gn <= tol * max(g0, 1e-300):
+            break
+        u -= np.linalg.lstsq(K, g, rcond=1e-12)[0]
+        steps += 1
+    Fs = element_F(u)
+    Pbar = np.zeros((D, D))
+    for F in Fs:
+        Pbar += np.einsum("eik,ekj->ij", F, pk(F, Ev)) / (N * len(Fs))
+    Farr = np.stack([F.transpose(1, 2, 0) for F in Fs])                 # (n_q, D, D, N)
+    return Farr, Pbar, steps

@@ -32,7 +32,9 @@ least-squares compatible part built from O2's real-space shape-function
 gradients, the law against central differences and frame indifference, the
 homogeneous cell (exact, no iteration), the small-strain limit (O1's C_eff),
 a grid-aligned laminate under stretch against its one-dimensional solution,
-and frame indifference of the whole cell solution.
+frame indifference of the whole cell solution, and equality with the
+periodic finite-strain FE problem assembled and solved in real space
+(``fem_assembly.finite_strain_fem``).
 """
 from __future__ import annotations
 

@@ -10,7 +10,9 @@ What fixes it without O3 itself:
   stress is O1's small-strain C_eff applied to the strain;
 * a grid-aligned laminate stretched along x matches its one-dimensional
   solution (closed_forms.laminate_stretch); rotating F_macro rotates the mean
-  stress of a heterogeneous cell.
+  stress of a heterogeneous cell;
+* the whole solve equals a Newton solve of the periodic finite-strain FE
+  problem assembled in real space (fem_assembly.finite_strain_fem).
 """
 import numpy as np
 import pytest
@@ -117,3 +119,18 @@ def test_rotated_load_rotates_mean_stress():
     F1, _, _, _ = P.solve(Fm, tol=1e-12)
     F2, _, _, _ = P.solve(R @ Fm, tol=1e-12)
     assert np.abs(P.mean_stress(F2) - R @ P.mean_stress(F1)).max() < 1e-9 * np.abs(P.mean_stress(F1)).max()
+
+
+@pytest.mark.parametrize("n,Fm", [((6, 5), [[1.1, 0.05], [-0.02, 0.95]]),
+                                  ((3, 4, 3), [[1.06, 0.02, 0.0], [0.0, 0.97, 0.03], [-0.02, 0.0, 1.03]])])
+def test_equals_real_space_finite_strain_fem(n, Fm):
+    """O3 (projection, Fourier space) against a Newton solve of the assembled
+    periodic finite-strain FE problem in real space (O2's shape functions)."""
+    from oracle.fem_assembly import finite_strain_fem
+    E = np.exp(np.random.default_rng(56).standard_normal(array_shape(n)))
+    P = FiniteStrainProblem(n, E, 0.3)
+    F, _, _, _ = P.solve(np.array(Fm), tol=1e-13)
+    F_fem, P_fem, steps = finite_strain_fem(n, E, 0.3, Fm)
+    assert steps >= 2
+    assert np.abs(P.mean_stress(F) - P_fem).max() < 1e-11 * np.abs(P_fem).max()
+    assert np.abs(F.reshape(F_fem.shape) - F_fem).max() < 1e-10
