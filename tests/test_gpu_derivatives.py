@@ -101,3 +101,19 @@ def test_rules_and_switching_back():
         r.set_derivative("fe")
         r.solve(np.eye(3), rel_tol=1e-12, max_iter=3000)
         assert rel_max(r.effective_tangent(), C_fe) < 1e-13
+
+
+@pytest.mark.parametrize("derivative", ["fourier", "lsq"])
+def test_anisotropic_voxels(derivative):
+    """Cell lengths enter the symbols through h_a = L_a / n_a."""
+    from paper_2105_03297_gb300 import RVE
+    n, length = (32, 16), (2.0, 0.5)
+    E = lognormal(n, 606)
+    C_ref, _, _ = Problem(n, E, 0.3, length=length, derivative=derivative).effective_tangent(np.eye(3), tol=1e-13)
+    with RVE(n, precision="fp64", length=length) as r:
+        r.set_derivative(derivative)
+        r.set_material(E, 0.3)
+        code, info = r.solve(np.eye(3), rel_tol=1e-12, max_iter=4000)
+        assert code == 0, info
+        C = r.effective_tangent()
+    assert rel_max(C, C_ref) < 1e-9

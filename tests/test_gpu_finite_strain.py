@@ -110,3 +110,19 @@ def test_rules():
         r.set_kinematics("small")
         code, _ = r.solve(np.eye(3), rel_tol=1e-10)
         assert code == 0
+
+
+def test_anisotropic_voxels():
+    from paper_2105_03297_gb300 import RVE
+    n, length = (32, 16), (2.0, 0.5)
+    E = lognormal(n, 705)
+    Fm = np.array([[1.07, 0.03], [0.0, 0.96]])
+    P = FiniteStrainProblem(n, E, 0.3, length=length)
+    F_ref, _, _, _ = P.solve(Fm, tol=1e-12)
+    with RVE(n, precision="fp64", length=length) as r:
+        r.set_kinematics("finite")
+        r.set_material(E, 0.3)
+        code, info = r.solve_finite(Fm[None], rel_tol=1e-12)
+        assert code == 0, info
+        Pm = r.mean_piola()[0]
+    assert rel_max(Pm, P.mean_stress(F_ref)) < 1e-9
