@@ -8,10 +8,7 @@ namespace rve {
 constexpr int kNT = 256;
 
 cudaError_t launch_residual(const Fp64Args& a, cudaStream_t s) {
-  dim3 grid((unsigned)((a.N + kNT - 1) / kNT), a.L);
-  if (a.dim == 2) residual_2d<kNT><<<grid, kNT, 0, s>>>(a);
-  else return launch_residual_3d(a, s);
-  return cudaGetLastError();
+  return a.dim == 2 ? launch_residual_2d(a, s) : launch_residual_3d(a, s);
 }
 
 int homogenise_blocks(const Fp64Args& a) { return (int)((a.N + kNT - 1) / kNT); }
