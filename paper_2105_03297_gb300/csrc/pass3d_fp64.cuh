@@ -48,115 +48,185 @@ __device__ __forceinline__ void stress_3d(const double* eps, double e, double la
   for (int j = 3; j < 6; ++j) sig[j] = e * mu2 * eps[j];
 }
 
-constexpr int kRTX = 16, kRTY = 4, kRTZ = 4;
-constexpr int kRVox = (kRTX + 1) * (kRTY + 1) * (kRTZ + 1);
+// f = B^T C (E + B u) per node, its squared norm, the squared norm of the
+// summed term magnitudes (round-off scale) and the copy of f in the inner
+// precision.  A block sweeps a node tile of (at most) 32 x 8 nodes through a
+// z-chunk of (at most) 16 planes: per voxel plane it loads the displacements
+// of the next node plane into shared memory, computes every voxel's corner
+// forces and term magnitudes once (plus a one-voxel halo on the low side), and
+// each node sums the 8 voxels it is a corner of.  grid (n_x/tx, n_y/ty,
+// (n_z/tz) L), kR3NT threads, residual_3d_smem() bytes.
+constexpr int kR3X = 32, kR3Y = 8, kR3Z = 16;
+constexpr int kR3NES = (kR3X + 2) * (kR3Y + 2);   // 340 nodes (both halos in x and y)
+constexpr int kR3VS = (kR3X + 1) * (kR3Y + 1);    // 297 voxels (low halo)
+constexpr int kR3NT = 352;
+static_assert(kR3NT >= kR3NES && kR3NT >= kR3VS, "one thread per node and per voxel of the tile");
+constexpr size_t residual_3d_smem() { return sizeof(double) * (2 * 3 * kR3NES + 2 * 3 * 12 * kR3VS); }
 
-// Tiled gather: each block computes the corner forces of the voxels of its
-// node tile plus a one-voxel halo on the low side (shared memory), then every
-// node sums the contributions of the 8 voxels it is a corner of.
-// grid (n_x/16, n_y/4, (n_z/4) * L), 256 threads.
-__global__ void __launch_bounds__(256) residual_3d(Fp64Args a) {
+__global__ void __launch_bounds__(kR3NT, 1) residual_3d(Fp64Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* contrib = reinterpret_cast<double*>(smem_raw);  // [kRVox][8][3]
-  double* cabs = contrib + kRVox * 24;                    // [kRVox][8][3] magnitudes
-  __shared__ double red[8];
+  double* un = reinterpret_cast<double*>(smem_raw);   // [2][3][kR3NES]: u of two node planes
+  double* lo = un + 2 * 3 * kR3NES;                   // [12][kR3VS]: corners dz = 0, current voxel plane
+  double* hi = lo + 12 * kR3VS;                       // [2][12][kR3VS]: corners dz = 1, current / previous
+  double* loa = hi + 2 * 12 * kR3VS;                  // magnitudes, same layout
+  double* hia = loa + 12 * kR3VS;
+  __shared__ double red[kR3NT / 32];
   __shared__ int flag;
-  const int nzt = a.n[2] / kRTZ;
-  const int l = blockIdx.z / nzt, tz = blockIdx.z % nzt;
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int tx = nx < kR3X ? nx : kR3X, ty = ny < kR3Y ? ny : kR3Y, tz = nz < kR3Z ? nz : kR3Z;
+  const int etx = tx + 2, nnode = (tx + 2) * (ty + 2);
+  const int vtx = tx + 1, nvox = (tx + 1) * (ty + 1);
+  const int nzc = nz / tz;
+  const int l = blockIdx.z / nzc, zc = blockIdx.z % nzc;
   CgState* cg = a.cg + l;
   if (!cg->active) return;
-  const int x0 = blockIdx.x * kRTX, y0 = blockIdx.y * kRTY, z0 = tz * kRTZ;
-  const double* u = a.u + (int64_t)l * 3 * a.N;
+  const int64_t N = a.N;
+  const int x0 = blockIdx.x * tx, y0 = blockIdx.y * ty, z0 = zc * tz;
+  const int tid = threadIdx.x;
+  const double* u = a.u + (int64_t)l * 3 * N;
   const double* em = a.emac + l * 6;
-  for (int i = threadIdx.x; i < kRVox; i += blockDim.x) {
-    const int ex = i % (kRTX + 1), ey = (i / (kRTX + 1)) % (kRTY + 1), ez = i / ((kRTX + 1) * (kRTY + 1));
-    const int vx = (x0 - 1 + ex) & (a.n[0] - 1);
-    const int vy = (y0 - 1 + ey) & (a.n[1] - 1);
-    const int vz = (z0 - 1 + ez) & (a.n[2] - 1);
-    double eps[6][6];
-    strain_3d(u, a.N, a.n, vx, vy, vz, em, a.ih, eps);
-    const double e = a.E[(int64_t)(l / a.lcs) * a.N + ((int64_t)vz * a.n[1] + vy) * a.n[0] + vx];
-    double f[8][3], fa[8][3];
+  const double* Eb = a.E + (int64_t)(l / a.lcs) * N;
+  const int64_t plane = (int64_t)nx * ny;
+  // node of the extended node tile (load) and voxel of the extended voxel tile
+  const int nex = tid % etx, ney = tid / etx;
+  const int64_t node_xy = (int64_t)((y0 - 1 + ney) & (ny - 1)) * nx + ((x0 - 1 + nex) & (nx - 1));
+  const int vex = tid % vtx, vey = tid / vtx;
+  const int64_t vox_xy = (int64_t)((y0 - 1 + vey) & (ny - 1)) * nx + ((x0 - 1 + vex) & (nx - 1));
+
+  auto load_plane = [&](int pz, double* dst) {
+    if (tid < nnode) {
+      const int64_t node = (int64_t)((z0 + pz) & (nz - 1)) * plane + node_xy;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) f[c][0] = f[c][1] = f[c][2] = fa[c][0] = fa[c][1] = fa[c][2] = 0.0;
-#pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      double s[6];
-      stress_3d(eps[t], e, a.lam, a.mu2, s);
-      double S[3][3];
-      S[0][0] = s[0]; S[1][1] = s[1]; S[2][2] = s[2];
-      S[1][2] = S[2][1] = kInvSqrt2 * s[3];
-      S[0][2] = S[2][0] = kInvSqrt2 * s[4];
-      S[0][1] = S[1][0] = kInvSqrt2 * s[5];
-      const int pa = kuhn_perm(t, 0), pb = kuhn_perm(t, 1), pc = kuhn_perm(t, 2);
-      const int v1 = 1 << pa, v2 = v1 | (1 << pb);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double Pa = a.ih[pa] * S[pa][j], Pb = a.ih[pb] * S[pb][j], Pc = a.ih[pc] * S[pc][j];
-        f[0][j] -= Pa;
-        f[v1][j] += Pa - Pb;
-        f[v2][j] += Pb - Pc;
-        f[7][j] += Pc;
-        fa[0][j] += fabs(Pa);
-        fa[v1][j] += fabs(Pa) + fabs(Pb);
-        fa[v2][j] += fabs(Pb) + fabs(Pc);
-        fa[7][j] += fabs(Pc);
-      }
+      for (int j = 0; j < 3; ++j) dst[j * kR3NES + tid] = u[j * N + node];
     }
+  };
+  load_plane(-1, un);
+  double acc = 0.0, acca = 0.0;
+  int cur = 0;
+  for (int zz = -1; zz < tz; ++zz) {
+    load_plane(zz + 1, un + ((zz + 2) & 1) * 3 * kR3NES);
+    __syncthreads();
+    if (tid < nvox) {
+      const double* p0 = un + ((zz + 1) & 1) * 3 * kR3NES;   // node plane zz
+      const double* p1 = un + ((zz + 2) & 1) * 3 * kR3NES;   // node plane zz + 1
+      double uc[8][3];
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+      for (int c = 0; c < 8; ++c) {
+        const int i = (vey + ((c >> 1) & 1)) * etx + vex + (c & 1);
+        const double* src = (c & 4) ? p1 : p0;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        contrib[(i * 8 + c) * 3 + j] = f[c][j];
-        cabs[(i * 8 + c) * 3 + j] = fa[c][j];
+        for (int j = 0; j < 3; ++j) uc[c][j] = src[j * kR3NES + i];
       }
-  }
-  __syncthreads();
-  const int lx = threadIdx.x % kRTX, ly = (threadIdx.x / kRTX) % kRTY, lz = threadIdx.x / (kRTX * kRTY);
-  double fn[3] = {0, 0, 0}, fna[3] = {0, 0, 0};
+      const double e = Eb[(int64_t)((z0 + zz) & (nz - 1)) * plane + vox_xy];
+      double f[8][3], fa[8][3];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-    const int ex = lx + 1 - dx, ey = ly + 1 - dy, ez = lz + 1 - dz;
-    const int i = (ez * (kRTY + 1) + ey) * (kRTX + 1) + ex;
+      for (int c = 0; c < 8; ++c) f[c][0] = f[c][1] = f[c][2] = fa[c][0] = fa[c][1] = fa[c][2] = 0.0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      fn[j] += contrib[(i * 8 + c) * 3 + j];
-      fna[j] += cabs[(i * 8 + c) * 3 + j];
+      for (int t = 0; t < 6; ++t) {
+        const int pa = kuhn_perm(t, 0), pb = kuhn_perm(t, 1), pc = kuhn_perm(t, 2);
+        const int v1 = 1 << pa, v2 = v1 | (1 << pb);
+        double H[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          H[pa][j] = (uc[v1][j] - uc[0][j]) * a.ih[pa];
+          H[pb][j] = (uc[v2][j] - uc[v1][j]) * a.ih[pb];
+          H[pc][j] = (uc[7][j] - uc[v2][j]) * a.ih[pc];
+        }
+        double eps[6], sg[6];
+        eps[0] = em[0] + H[0][0];
+        eps[1] = em[1] + H[1][1];
+        eps[2] = em[2] + H[2][2];
+        eps[3] = em[3] + kInvSqrt2 * (H[1][2] + H[2][1]);
+        eps[4] = em[4] + kInvSqrt2 * (H[0][2] + H[2][0]);
+        eps[5] = em[5] + kInvSqrt2 * (H[0][1] + H[1][0]);
+        stress_3d(eps, e, a.lam, a.mu2, sg);
+        double S[3][3];
+        S[0][0] = sg[0]; S[1][1] = sg[1]; S[2][2] = sg[2];
+        S[1][2] = S[2][1] = kInvSqrt2 * sg[3];
+        S[0][2] = S[2][0] = kInvSqrt2 * sg[4];
+        S[0][1] = S[1][0] = kInvSqrt2 * sg[5];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const double Pa = a.ih[pa] * S[pa][j], Pb = a.ih[pb] * S[pb][j], Pc = a.ih[pc] * S[pc][j];
+          f[0][j] -= Pa;
+          f[v1][j] += Pa - Pb;
+          f[v2][j] += Pb - Pc;
+          f[7][j] += Pc;
+          fa[0][j] += fabs(Pa);
+          fa[v1][j] += fabs(Pa) + fabs(Pb);
+          fa[v2][j] += fabs(Pb) + fabs(Pc);
+          fa[7][j] += fabs(Pc);
+        }
+      }
+      double* hc = hi + cur * 12 * kR3VS;
+      double* hca = hia + cur * 12 * kR3VS;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          lo[(c * 3 + j) * kR3VS + tid] = f[c][j];
+          loa[(c * 3 + j) * kR3VS + tid] = fa[c][j];
+          hc[(c * 3 + j) * kR3VS + tid] = f[c + 4][j];
+          hca[(c * 3 + j) * kR3VS + tid] = fa[c + 4][j];
+        }
     }
-  }
-  const int64_t node = ((int64_t)(z0 + lz) * a.n[1] + (y0 + ly)) * a.n[0] + x0 + lx;
-  if (a.fout_f32) {
-    float* fo = (float*)a.fout + (int64_t)l * 3 * a.N;
+    __syncthreads();
+    if (zz >= 0 && tid < tx * ty) {
+      // node (x0 + lx, y0 + ly, z0 + zz): corner (dx, dy, dz) of voxel (x - dx, y - dy, z - dz)
+      const int lx = tid % tx, ly = tid / tx;
+      const double* hp = hi + (cur ^ 1) * 12 * kR3VS;
+      const double* hpa = hia + (cur ^ 1) * 12 * kR3VS;
+      double fn[3] = {0, 0, 0}, fna[3] = {0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) fo[j * a.N + node] = (float)fn[j];
-  } else {
-    double* fo = (double*)a.fout + (int64_t)l * 3 * a.N;
+      for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) fo[j * a.N + node] = fn[j];
+        for (int dx = 0; dx < 2; ++dx) {
+          const int i = (ly + 1 - dy) * vtx + (lx + 1 - dx);
+          const int c = dx + 2 * dy;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            fn[j] += lo[(c * 3 + j) * kR3VS + i] + hp[(c * 3 + j) * kR3VS + i];
+            fna[j] += loa[(c * 3 + j) * kR3VS + i] + hpa[(c * 3 + j) * kR3VS + i];
+          }
+        }
+      const int64_t node = ((int64_t)(z0 + zz) * ny + (y0 + ly)) * nx + x0 + lx;
+      if (a.fout_f32) {
+        float* fo = (float*)a.fout + (int64_t)l * 3 * N;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) fo[j * N + node] = (float)fn[j];
+      } else {
+        double* fo = (double*)a.fout + (int64_t)l * 3 * N;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) fo[j * N + node] = fn[j];
+      }
+      acc += fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2];
+      acca += fna[0] * fna[0] + fna[1] * fna[1] + fna[2] * fna[2];
+    }
+    cur ^= 1;
+    __syncthreads();
   }
-  const double acc = fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2];
-  const double acca = fna[0] * fna[0] + fna[1] * fna[1] + fna[2] * fna[2];
-  const double s = block_sum<256>(acc, red);
-  const double sa = block_sum<256>(acca, red);
-  const int nblk = gridDim.x * gridDim.y * nzt;
-  const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * tz);
+  const double s = block_sum<kR3NT>(acc, red);
+  const double sa = block_sum<kR3NT>(acca, red);
+  const int nblk = gridDim.x * gridDim.y * nzc;
+  const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc);
   double* part = a.part + (int64_t)l * a.part_stride;
   double* parta = part + a.part_stride / 2;
   if (threadIdx.x == 0) parta[blk] = sa;
   if (publish_partial(s, part, &cg->cnt_r, blk, nblk, &flag)) {
-    const double t = sum_partials<256>(part, nblk, red);
-    const double ta = sum_partials<256>(parta, nblk, red);
+    const double t = sum_partials<kR3NT>(part, nblk, red);
+    const double ta = sum_partials<kR3NT>(parta, nblk, red);
     if (threadIdx.x == 0) { cg->fn2 = t; cg->fa2 = ta; cg->cnt_r = 0; }
   }
 }
 
 inline cudaError_t launch_residual_3d(const Fp64Args& a, cudaStream_t s) {
-  const size_t sm = sizeof(double) * kRVox * 48;
+  const int tx = a.n[0] < kR3X ? a.n[0] : kR3X, ty = a.n[1] < kR3Y ? a.n[1] : kR3Y;
+  const int tz = a.n[2] < kR3Z ? a.n[2] : kR3Z;
+  const size_t sm = residual_3d_smem();
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(residual_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
-  dim3 grid(a.n[0] / kRTX, a.n[1] / kRTY, (a.n[2] / kRTZ) * a.L);
-  residual_3d<<<grid, 256, sm, s>>>(a);
+  dim3 grid(a.n[0] / tx, a.n[1] / ty, (a.n[2] / tz) * a.L);
+  residual_3d<<<grid, kR3NT, sm, s>>>(a);
   return cudaGetLastError();
 }
 

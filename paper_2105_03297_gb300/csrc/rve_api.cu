@@ -177,6 +177,15 @@ template <typename T> std::vector<T> phase_table(int n, int sgn) {
   return t;
 }
 
+// Copies and fills go on the handle's stream, which is non-blocking: a call on
+// the legacy default stream would not be ordered with the kernels launched on
+// it (a fill could still be running when the first kernel writes the buffer).
+int copy_sync(rve_s* h, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  CK(cudaMemcpyAsync(dst, src, bytes, kind, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
 template <typename T> int upload_tables(rve_s* h) {
   for (int a = 0; a < h->dim; ++a) {
     const int n = h->n[a];
@@ -185,8 +194,8 @@ template <typename T> int upload_tables(rve_s* h) {
     if (rc) return rc;
     rc = dev_alloc(&h->tw[a], tw.size() * sizeof(T));
     if (rc) return rc;
-    CK(cudaMemcpy(h->ph[a], ph.data(), ph.size() * sizeof(T), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->tw[a], tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if ((rc = copy_sync(h, h->ph[a], ph.data(), ph.size() * sizeof(T), cudaMemcpyHostToDevice))) return rc;
+    if ((rc = copy_sync(h, h->tw[a], tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice))) return rc;
   }
   return RVE_OK;
 }
@@ -220,7 +229,11 @@ int ensure_capacity(rve_s* h, int L) {
       h->u = old_u;
       return RVE_ERR_OOM;
     }
-    cudaMemcpy(keep_u, old_u, (size_t)oldL * h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (int rc = copy_sync(h, keep_u, old_u, (size_t)oldL * h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice)) {
+      cudaFree(keep_u);
+      h->u = old_u;
+      return rc;
+    }
   }
   if (old_u) cudaFree(old_u);
   free_L(h);
@@ -247,14 +260,15 @@ int ensure_capacity(rve_s* h, int L) {
       cudaMallocHost((void**)&h->cg_h2, (size_t)Lp * sizeof(CgState)) != cudaSuccess) {
     cudaGetLastError(); free_L(h); if (keep_u) cudaFree(keep_u); return RVE_ERR_OOM;
   }
-  cudaMemset(h->p, 0, fld);
-  if (h->p2) cudaMemset(h->p2, 0, fld);
-  cudaMemset(h->x, 0, fld);
-  cudaMemset(h->part, 0, (size_t)Lp * h->part_stride * sizeof(double));
-  if (keep_u) {
-    cudaMemcpy(h->u, keep_u, (size_t)oldL * h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice);
-    cudaFree(keep_u);
-  }
+  cudaMemsetAsync(h->p, 0, fld, h->stream);
+  if (h->p2) cudaMemsetAsync(h->p2, 0, fld, h->stream);
+  cudaMemsetAsync(h->x, 0, fld, h->stream);
+  cudaMemsetAsync(h->part, 0, (size_t)Lp * h->part_stride * sizeof(double), h->stream);
+  if (keep_u)
+    cudaMemcpyAsync(h->u, keep_u, (size_t)oldL * h->D * h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  const cudaError_t se = cudaStreamSynchronize(h->stream);
+  if (keep_u) cudaFree(keep_u);
+  CK(se);
   h->Lcap = L;
   CK(cudaGetLastError());
   return RVE_OK;
@@ -993,7 +1007,7 @@ int read_moduli(int64_t N, const void* E, int E_dtype, int ptr_flags, std::vecto
 // Upload field `slot` (FP64 host copy) and its inner-precision copy.
 int upload_material(rve_s* h, int slot, const std::vector<double>& e64) {
   double* dst = h->E64 + (size_t)slot * h->N;
-  CK(cudaMemcpy(dst, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice));
+  if (int rc = copy_sync(h, dst, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice)) return rc;
   if (h->precision == RVE_MIXED) {
     f32_from_f64<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(dst, (float*)h->Ein + (size_t)slot * h->N,
                                                                           h->N);
@@ -1144,7 +1158,7 @@ int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_fla
     else for (int64_t i = 0; i < h->N; ++i) e64[i] = ((const float*)E)[i];
   }
   if (int rc = check_moduli(e64)) return rc;
-  CK(cudaMemcpy(h->E64, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice));
+  if (int rc = copy_sync(h, h->E64, e64.data(), (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice)) return rc;
   if (h->precision == RVE_MIXED) {
     f32_from_f64<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->E64, (float*)h->Ein, h->N);
     CK(cudaGetLastError());
@@ -1376,7 +1390,8 @@ int rve_set_operator_form(rve_t h, int form) {
   if (form == RVE_FORM_FACTORED && h->Lcap > 0 && !h->p2) {
     const size_t fld = (size_t)h->Lcap * h->m * h->N * h->tsize;
     if (int rc = dev_alloc(&h->p2, fld)) return rc;
-    CK(cudaMemset(h->p2, 0, fld));
+    CK(cudaMemsetAsync(h->p2, 0, fld, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
   }
   h->op_form = form;
   return RVE_OK;
