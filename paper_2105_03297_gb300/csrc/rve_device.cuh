@@ -296,6 +296,22 @@ template <typename T> __device__ __forceinline__ void vload(T* d, const T* s) {
 #pragma unroll
   for (int i = 0; i < Vec16<T>::n; ++i) d[i] = a[i];
 }
+// Bulk prefetch into L2 by the TMA unit (no data reaches the SM): `bytes` a
+// multiple of 16 starting at a 16-byte aligned global address.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// Prefetch `rows` contiguous rows of NX values, `rows_per_comp` per component
+// (components comp_stride apart): one bulk request per row.
+template <typename T, int NX>
+__device__ __forceinline__ void prefetch_rows_l2(const T* base, int comps, int rows_per_comp, int64_t comp_stride) {
+  static_assert((NX * sizeof(T)) % 16 == 0, "bulk prefetch sizes are multiples of 16 bytes");
+  for (int i = threadIdx.x; i < comps * rows_per_comp; i += blockDim.x) {
+    const int j = i / rows_per_comp, row = i % rows_per_comp;
+    prefetch_l2_bulk(base + j * comp_stride + (int64_t)row * NX, (unsigned)(NX * sizeof(T)));
+  }
+}
+
 // Two consecutive complex values (16 bytes for float, two 16-byte halves for double)
 template <typename T> __device__ __forceinline__ void cload2(cplx<T>* d, const cplx<T>* s) {
   if constexpr (sizeof(T) == 4) {
