@@ -93,6 +93,11 @@ const char* rve_error_string(int code);
  *              material in FP32 inside an FP64 iterative refinement on the nodal
  *              displacement (CG scalars and reductions in FP64);
  *  cuda_stream a cudaStream_t (NULL = default stream).
+ * The handle runs its work on a non-blocking stream of its own, which every
+ * call first orders after cuda_stream (device data the caller wrote there is
+ * seen); every call that returns results (solve, means, fields, operator
+ * application) returns after its device work has completed.  Calls on one
+ * handle must not run concurrently from several host threads.
  * Allocates device memory for one load case; more is allocated by rve_solve. */
 int rve_create(rve_t* out, int dim, const int64_t* n, const double* length,
                int precision, void* cuda_stream);
