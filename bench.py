@@ -14,6 +14,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -214,6 +215,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_cpu(cpuinfo=None):
+    """CPU model and logical core count of this host (for the CPU baseline).
+
+    x86 lists a "model name"; Arm lists "CPU part" codes (and sometimes "Model")."""
+    model = None
+    try:
+        if cpuinfo is None:
+            with open("/proc/cpuinfo") as f:
+                cpuinfo = f.read()
+        info = cpuinfo
+        for key in ("model name", "Model", "CPU part"):
+            for ln in info.splitlines():
+                if ln.split(":")[0].strip() == key:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+            if model:
+                model = model if key != "CPU part" else f"{platform.machine()} CPU part {model}"
+                break
+    except OSError:
+        pass
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def oracle_sample(cfg_name, seconds_budget=20.0):
     """Time the FP64 oracle's CG iterations on this host (bounded sample).
 
@@ -284,7 +308,8 @@ def run_reference(args):
         "ms_per_cg_iteration": ms_it,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sample_its} FP64 CG iterations of one load case of {cfg_name} "
-                                   f"(numpy oracle), scaled by the {total_its} iterations of the full solve"},
+                                   f"(numpy oracle), scaled by the {total_its} iterations of the full solve",
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -522,7 +547,8 @@ def run_gpu(args):
         v = 1.0 / (sec_it * total_its)
         out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
                                "sample": f"{its} FP64 CG iterations of one load case (numpy oracle, "
-                                         f"{sec_it * 1e3:.0f} ms each), scaled by {total_its} iterations per solve"}
+                                         f"{sec_it * 1e3:.0f} ms each), scaled by {total_its} iterations per solve",
+                               "host": host_cpu()}
     if rank == 0:
         print(json.dumps(out), flush=True)
     r.close()

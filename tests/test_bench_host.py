@@ -36,3 +36,12 @@ def test_traffic_rows_follow_the_kernel_hash():
         else:
             assert got is None
     assert bench.measured_traffic("gauss1024", "stress", "no_such_pass", 2) is None
+
+
+def test_host_cpu_description():
+    h = bench.host_cpu()
+    assert isinstance(h["model"], str) and h["model"] and h["nproc"] >= 1
+    x86 = "processor\t: 0\nmodel name\t: Some CPU @ 3.0GHz\nflags\t: fpu\n"
+    assert bench.host_cpu(x86)["model"] == "Some CPU @ 3.0GHz"
+    arm = "processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n"
+    assert bench.host_cpu(arm)["model"].endswith("CPU part 0xd4f")
