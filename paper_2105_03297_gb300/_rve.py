@@ -110,17 +110,32 @@ def _check(code, where, allow=()):
     return code
 
 
-def _dptr(arr):
-    """(pointer, flag, keepalive) of a numpy array or a CUDA torch tensor."""
+def _buffer(arr, dtype, count, name):
+    """(pointer, flag, keepalive) of a buffer of which the library reads or
+    writes ``count`` elements of ``dtype``: a C-contiguous numpy array (host)
+    or a contiguous torch tensor (device or host).  A wrong element type, size
+    or layout raises here, before the library touches the memory."""
+    dtype = np.dtype(dtype)
     if isinstance(arr, np.ndarray):
+        if arr.dtype != dtype:
+            raise TypeError(f"{name}: dtype {arr.dtype}, expected {dtype}")
+        if not arr.flags.c_contiguous:
+            raise ValueError(f"{name}: array must be C-contiguous")
+        if arr.size != count:
+            raise ValueError(f"{name}: {arr.size} elements, expected {count}")
         return arr.ctypes.data_as(C.c_void_p), RVE_PTR_HOST, arr
     import torch
     if isinstance(arr, torch.Tensor):
+        want = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64}[dtype]
+        if arr.dtype != want:
+            raise TypeError(f"{name}: dtype {arr.dtype}, expected {want}")
         if not arr.is_contiguous():
-            raise ValueError("tensor must be contiguous")
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if arr.numel() != count:
+            raise ValueError(f"{name}: {arr.numel()} elements, expected {count}")
         flag = RVE_PTR_DEVICE if arr.is_cuda else RVE_PTR_HOST
         return C.c_void_p(arr.data_ptr()), flag, arr
-    raise TypeError(type(arr))
+    raise TypeError(f"{name}: expected a numpy array or a torch tensor, got {type(arr).__name__}")
 
 
 class RVE:
@@ -162,21 +177,26 @@ class RVE:
         self.close()
 
     def set_material(self, E, nu):
+        """Per-voxel Young's moduli E (N values, x fastest: numpy array or torch
+        tensor, float32 or float64) and the Poisson ratio nu."""
         if isinstance(E, np.ndarray):
             E = np.ascontiguousarray(E)
-            dt = RVE_F32 if E.dtype == np.float32 else RVE_F64
             if E.dtype not in (np.float32, np.float64):
-                E = E.astype(np.float64); dt = RVE_F64
+                E = E.astype(np.float64)
+            dtype = E.dtype
         else:
             import torch
-            dt = RVE_F32 if E.dtype == torch.float32 else RVE_F64
-        assert int(np.prod(E.shape)) == self.N
-        p, flag, _keep = _dptr(E)
+            if not isinstance(E, torch.Tensor) or E.dtype not in (torch.float32, torch.float64):
+                raise TypeError("E: expected a float32 or float64 numpy array or torch tensor")
+            dtype = np.float32 if E.dtype == torch.float32 else np.float64
+        p, flag, _keep = _buffer(E, dtype, self.N, "E")
+        dt = RVE_F32 if np.dtype(dtype) == np.float32 else RVE_F64
         _check(load().rve_set_material(self.h, p, dt, float(nu), flag), "rve_set_material")
 
     def solve(self, E_macro, rel_tol=1e-10, max_iter=5000):
         Em = np.ascontiguousarray(np.atleast_2d(np.asarray(E_macro, dtype=np.float64)))
-        assert Em.shape[1] == self.ns
+        if Em.ndim != 2 or Em.shape[1] != self.ns:
+            raise ValueError(f"E_macro: shape {Em.shape}, expected (L, {self.ns})")
         L = Em.shape[0]
         info = (rve_info * L)()
         code = load().rve_solve(self.h, Em.ctypes.data_as(C.POINTER(C.c_double)), L, float(rel_tol),
@@ -204,9 +224,11 @@ class RVE:
 
     def adjoint(self, W, rel_tol=1e-10, max_iter=5000, out=None):
         W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+        if W.shape != (self.ns, self.ns):
+            raise ValueError(f"W: shape {W.shape}, expected ({self.ns}, {self.ns})")
         if out is None:
             out = np.zeros(self.N)
-        p, flag, _keep = _dptr(out)
+        p, flag, _keep = _buffer(out, np.float64, self.N, "out")
         code = load().rve_adjoint(self.h, W.ctypes.data_as(C.POINTER(C.c_double)), float(rel_tol),
                                   int(max_iter), p, flag)
         _check(code, "rve_adjoint", allow=(RVE_ERR_NOT_CONVERGED,))
@@ -215,7 +237,7 @@ class RVE:
     def get_strain(self, load_case, out=None):
         if out is None:
             out = np.zeros((self.m, self.N))
-        p, flag, _keep = _dptr(out)
+        p, flag, _keep = _buffer(out, np.float64, self.m * self.N, "out")
         _check(load().rve_get_strain(self.h, int(load_case), p, flag), "rve_get_strain")
         return out
 
@@ -289,7 +311,7 @@ class RVE:
     def get_deformation(self, load_case):
         nq = 2 if self.dim == 2 else 6
         out = np.zeros((nq, self.dim, self.dim, self.N))
-        p, flag, _k = _dptr(out)
+        p, flag, _k = _buffer(out, np.float64, out.size, "out")
         _check(load().rve_get_deformation(self.h, int(load_case), p, flag), "rve_get_deformation")
         return out
 
@@ -308,13 +330,17 @@ class RVE:
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KINDS)}
 
     def apply_operator(self, p, material=True, out=None):
+        """q = G C p (material=False: q = G p) for p[m][N] in the handle's inner
+        precision (numpy array or torch tensor; out of the same kind and place)."""
         if isinstance(p, np.ndarray):
             p = np.ascontiguousarray(p, dtype=self.inner_dtype)
-            if out is None:
-                out = np.zeros_like(p)
-        pp, flag, _k1 = _dptr(p)
-        qp, flag2, _k2 = _dptr(out)
-        assert flag == flag2
+        if out is None:
+            out = np.zeros_like(p) if isinstance(p, np.ndarray) else p.new_empty(p.shape)
+        count = self.m * self.N
+        pp, flag, _k1 = _buffer(p, self.inner_dtype, count, "p")
+        qp, flag2, _k2 = _buffer(out, self.inner_dtype, count, "out")
+        if flag != flag2:
+            raise ValueError("p and out must both be host or both be device buffers")
         _check(load().rve_apply_operator(self.h, pp, qp, 1 if material else 0, flag), "rve_apply_operator")
         return out
 
@@ -354,12 +380,19 @@ class RVEBatch:
         self.close()
 
     def set_material(self, index, E):
+        if not 0 <= int(index) < self.count:
+            raise IndexError(f"index {index} outside 0..{self.count - 1}")
         E = np.ascontiguousarray(E, dtype=np.float64)
+        want = int(np.prod(self.sizes[int(index)]))
+        if E.size != want:
+            raise ValueError(f"E: {E.size} elements, expected {want} for RVE {index}")
         _check(load().rve_batch_set_material(self.h, int(index), E.ctypes.data_as(C.c_void_p), RVE_F64,
                                              RVE_PTR_HOST), "rve_batch_set_material")
 
     def solve(self, E_macro, rel_tol=1e-10, max_iter=5000):
         Em = np.ascontiguousarray(np.atleast_2d(np.asarray(E_macro, dtype=np.float64)))
+        if Em.ndim != 2 or Em.shape[1] != self.ns:
+            raise ValueError(f"E_macro: shape {Em.shape}, expected (L, {self.ns})")
         L = Em.shape[0]
         info = (rve_info * (self.count * L))()
         code = load().rve_batch_solve(self.h, Em.ctypes.data_as(C.POINTER(C.c_double)), L, float(rel_tol),

@@ -1,0 +1,86 @@
+"""Argument marshalling of the Python binding (CPU, no device work): caller
+buffers of the wrong element type, size or layout are rejected before the
+library reads or writes them."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2105_03297_gb300 import _rve
+
+
+def test_buffer_accepts_exact_numpy_and_torch_buffers():
+    a = np.zeros((3, 5))
+    p, flag, keep = _rve._buffer(a, np.float64, 15, "a")
+    assert flag == _rve.RVE_PTR_HOST and keep is a and p.value == a.ctypes.data
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(15, dtype=torch.float32)
+    p, flag, keep = _rve._buffer(t, np.float32, 15, "t")
+    assert flag == _rve.RVE_PTR_HOST and p.value == t.data_ptr()
+
+
+@pytest.mark.parametrize("bad,err", [
+    (np.zeros(14), ValueError),                      # too small: the library would write past it
+    (np.zeros(15, dtype=np.float32), TypeError),     # wrong element type
+    (np.zeros((5, 6))[:, ::2], ValueError),          # 15 elements, not contiguous
+    ([0.0] * 15, TypeError),                         # not a buffer
+])
+def test_buffer_rejects_mismatches(bad, err):
+    with pytest.raises(err):
+        _rve._buffer(bad, np.float64, 15, "out")
+
+
+def test_buffer_rejects_torch_mismatches():
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        _rve._buffer(torch.zeros(15, dtype=torch.float16), np.float64, 15, "E")
+    with pytest.raises(ValueError):
+        _rve._buffer(torch.zeros(16, dtype=torch.float64), np.float64, 15, "E")
+    with pytest.raises(ValueError):
+        _rve._buffer(torch.zeros(5, 6, dtype=torch.float64)[:, ::2], np.float64, 15, "E")
+
+
+def _fake_handle(dim=2, n=(4, 4), precision="mixed"):
+    """An RVE object with sizes but a NULL handle: if a check were missing, the
+    library would see the NULL handle and return RVE_ERR_ARG, not touch memory."""
+    r = object.__new__(_rve.RVE)
+    r.n, r.dim, r.precision = n, dim, precision
+    r.N = int(np.prod(n)); r.ns = 3 if dim == 2 else 6; r.m = 2 * r.ns if dim == 2 else 6 * r.ns
+    r.inner_dtype = np.float32 if precision == "mixed" else np.float64
+    r.h = None
+    r.L = 0
+    return r
+
+
+def test_methods_check_their_buffers_first():
+    r = _fake_handle()
+    with pytest.raises(ValueError):
+        r.set_material(np.ones(15), 0.3)                       # N = 16
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        r.set_material(torch.ones(16, dtype=torch.float16), 0.3)
+    with pytest.raises(ValueError):
+        r.solve(np.eye(4))                                      # n_s = 3
+    with pytest.raises(ValueError):
+        r.adjoint(np.eye(3), out=np.zeros(15))
+    with pytest.raises(ValueError):
+        r.adjoint(np.eye(2))
+    with pytest.raises(ValueError):
+        r.get_strain(0, out=np.zeros((r.m, r.N - 1)))
+    with pytest.raises(TypeError):
+        r.get_strain(0, out=np.zeros((r.m, r.N), dtype=np.float32))
+    with pytest.raises(ValueError):
+        r.apply_operator(np.zeros((r.m - 1, r.N)))
+    with pytest.raises(TypeError):
+        r.apply_operator(np.zeros((r.m, r.N)), out=np.zeros((r.m, r.N)))   # out must be FP32 here
+    r.h = None
+
+
+def test_null_handle_is_an_argument_error():
+    lib = _rve.load()
+    assert lib.rve_solve(None, None, 1, 1e-10, 10, None) == _rve.RVE_ERR_ARG
+    assert lib.rve_set_material(None, None, _rve.RVE_F64, 0.3, _rve.RVE_PTR_HOST) == _rve.RVE_ERR_ARG
+    assert lib.rve_apply_operator(None, None, None, 1, 0) == _rve.RVE_ERR_ARG
+    assert lib.rve_get_strain(None, 0, None, 0) == _rve.RVE_ERR_ARG
+    assert isinstance(lib.rve_error_string(_rve.RVE_ERR_ARG), bytes)
+    assert C.sizeof(_rve.rve_info) == 32
