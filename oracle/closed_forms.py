@@ -70,7 +70,8 @@ def laminate_tangent(layer_E, nu, dim):
 
 
 def voigt_reuss(E_field, nu, dim):
-    """(Voigt, Reuss) Mandel bounds of a per-voxel isotropic field."""
+    """(Voigt, Reuss) Mandel bounds of a per-voxel isotropic field: any minimiser of
+    the energy of Eq. stat-mech-equi-weak-form lies between them."""
     Cbar = stiffness_mandel(dim, 1.0, nu)
     Ev = np.asarray(E_field).reshape(-1)
     voigt = Cbar * np.mean(Ev)
@@ -124,7 +125,8 @@ def appendix_b_projection(Dsym):
 def laminate_stretch(layer_E, nu, dim, stretch):
     """Mean first Piola-Kirchhoff stress of a grid-aligned laminate (layers
     normal to x, equal thickness) under F_macro = diag(stretch, 1, ...), for
-    the St. Venant-Kirchhoff law.
+    the St. Venant-Kirchhoff law (the finite-strain reading of Sec. 3.1); the
+    linear elements of Sec. 2.6 represent its exact solution.
 
     The exact solution keeps F = diag(f_k, 1, ...) in layer k (a piecewise
     linear u_x(x), which linear elements represent exactly); equilibrium makes
@@ -140,6 +142,7 @@ def laminate_stretch(layer_E, nu, dim, stretch):
     M1 = lam1 + 2.0 * mu1
 
     def f_of(P):
+        """Stretch f_k of every layer that carries the traction P_xx (Newton)."""
         f = np.full_like(E, 1.0)
         for _ in range(100):
             g = E * M1 * f * (f * f - 1.0) / 2.0 - P

@@ -48,44 +48,51 @@ SQRT2 = np.sqrt(2.0)
 # --------------------------------------------------------------------------
 
 def n_strain(dim):
-    """Number of independent symmetric strain components n_s."""
+    """Number of independent symmetric strain components n_s (the small-strain tensor of
+    Eq. small-strain, Appendix B)."""
     return 3 if dim == 2 else 6
 
 
 def n_elements(dim):
-    """Elements (= quadrature points) per voxel n_q."""
+    """Elements (= quadrature points) per voxel n_q: two triangles in 2D, six Kuhn
+    tetrahedra in 3D (Sec. 2.6)."""
     return 2 if dim == 2 else 6
 
 
 def mandel_pairs(dim):
-    """Tensor index pair (i, j) of each Mandel component."""
+    """Tensor index pair (i, j) of each Mandel component.  Mandel's sqrt2 on the shear
+    components makes the Euclidean product of Mandel vectors the double contraction
+    of the weak form (Eq. stat-mech-equi-weak-form), so G stays self-adjoint."""
     if dim == 2:
         return [(0, 0), (1, 1), (0, 1)]
     return [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
 
 
 def mandel_weight(i, j):
+    """sqrt2 on off-diagonal pairs, 1 on the diagonal (see mandel_pairs)."""
     return 1.0 if i == j else SQRT2
 
 
 def array_shape(n):
+    """Array shape of a per-voxel field on the grid of Appendix A (x fastest)."""
     return tuple(int(v) for v in reversed(tuple(n)))
 
 
 def voxel_size(n, length=None):
+    """Voxel edge lengths h_a = L_a / n_a of the grid of Appendix A (unit cell by default)."""
     if length is None:
         length = (1.0,) * len(n)
     return tuple(float(L) / int(na) for L, na in zip(length, n))
 
 
 def tensor_to_mandel(T):
-    """Symmetric tensors ``T[..., i, j]`` to Mandel vectors ``[..., s]``."""
+    """Symmetric tensors ``T[..., i, j]`` to Mandel vectors ``[..., s]`` (see mandel_pairs)."""
     dim = T.shape[-1]
     return np.stack([mandel_weight(i, j) * T[..., i, j] for i, j in mandel_pairs(dim)], axis=-1)
 
 
 def mandel_to_tensor(v, dim):
-    """Mandel vectors ``v[..., s]`` to symmetric tensors ``[..., i, j]``."""
+    """Mandel vectors ``v[..., s]`` to symmetric tensors ``[..., i, j]`` (see mandel_pairs)."""
     T = np.zeros(v.shape[:-1] + (dim, dim), dtype=v.dtype)
     for s, (i, j) in enumerate(mandel_pairs(dim)):
         T[..., i, j] = v[..., s] / mandel_weight(i, j)
@@ -98,7 +105,8 @@ def mandel_to_tensor(v, dim):
 # --------------------------------------------------------------------------
 
 def lame(E, nu):
-    """Lame constants (lambda, mu) from Young's modulus and Poisson's ratio."""
+    """Lame constants (lambda, mu) from Young's modulus and Poisson's ratio, the two
+    constants the examples give (Sec. 3.3)."""
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
     return lam, mu
@@ -107,7 +115,8 @@ def lame(E, nu):
 def stiffness_mandel(dim, E=1.0, nu=0.3):
     """Isotropic stiffness ``lambda 1(x)1 + 2 mu I`` as an n_s x n_s Mandel matrix.
 
-    In 2D this is plane strain: the in-plane block of the 3D tensor.
+    Isotropic linear elasticity in the constants of Sec. 3.3.  In 2D this is plane
+    strain (the paper does not say; our reading): the in-plane block of the 3D tensor.
     """
     lam, mu = lame(E, nu)
     ns = n_strain(dim)
@@ -122,7 +131,8 @@ def stiffness_mandel(dim, E=1.0, nu=0.3):
 
 
 def apply_material(field, E, nu):
-    """sigma_Theta = E_v * Cbar(nu) : eps_Theta for every element of every voxel.
+    """sigma_Theta = E_v * Cbar(nu) : eps_Theta for every element of every voxel
+    (one constant strain per element, Sec. 2.6; every element of a voxel has its modulus).
 
     ``field``: (m, *array_shape) Mandel strains; ``E``: (*array_shape) moduli.
     """
@@ -140,7 +150,8 @@ def apply_material(field, E, nu):
 # --------------------------------------------------------------------------
 
 def phase_factors(n):
-    """exp(i k_a h_a) = exp(2 pi i m_a / n_a) on the full FFT grid, per axis."""
+    """exp(i k_a h_a) = exp(2 pi i m_a / n_a) on the full FFT grid, per axis: the wave
+    vectors of Eq. Fourier_wave_vectors for the forward DFT of Eq. discrete-fourier-trafo."""
     D = len(n)
     out = []
     for a, na in enumerate(n):
@@ -255,7 +266,8 @@ def derivative_symbols(n, length=None, derivative="fe"):
 
 
 def strain_symbol(g):
-    """B(k): (*array_shape, m, D) complex, Fourier symbol of u -> sym(grad_Theta u).
+    """B(k): (*array_shape, m, D) complex, Fourier symbol of u -> sym(grad_Theta u),
+    the element strain of Eq. small-strain with the element derivatives g_Theta(k).
 
     Row Theta*n_s + s, column j is Mandel component s of sym(g_Theta (x) e_j).
     """
@@ -288,7 +300,8 @@ def projection_matrices(B):
 
 
 class Problem:
-    """A periodic RVE: grid, cell lengths, per-voxel moduli and Poisson ratio."""
+    """A periodic RVE (Sec. 2.1): grid of Appendix A, cell lengths, per-voxel moduli
+    and Poisson ratio, with the discrete derivative that defines B(k) (Sec. 2.3)."""
 
     def __init__(self, n, E, nu, length=None, derivative="fe"):
         self.n = tuple(int(v) for v in n)
@@ -316,7 +329,10 @@ class Problem:
 
     # -- the projection, applied in the factored form B (B^H B)^-1 B^H ----
     def project_hat(self, fh):
-        """Apply G(k) to a spectrum ``fh`` of shape (m, *shape); G(0) = 0."""
+        """Apply G(k) to a spectrum ``fh`` of shape (m, *shape); G(0) = 0 (Sec. 2.3).
+
+        G = B (B^H B)^-1 B^H is the small-strain projection of Appendix B
+        (Eqs. small-strain-eq2, small-strain-chi) in matrix form."""
         x = np.moveaxis(fh, 0, -1)[..., None]            # (*shape, m, 1)
         t = np.conj(np.swapaxes(self.B, -1, -2)) @ x      # B^H f
         u = np.linalg.solve(self.BHB, t)                  # (B^H B)^-1 B^H f
@@ -325,11 +341,13 @@ class Problem:
         return np.moveaxis(y, -1, 0)
 
     def project(self, f):
-        """Real-space projection F^-1[ G(k) F[f](k) ] of an (m, *shape) field."""
+        """Real-space projection F^-1[ G(k) F[f](k) ] of an (m, *shape) field, with the
+        DFT pair of Eqs. discrete-fourier-trafo and inverse-discrete-fourier-trafo."""
         fh = np.fft.fftn(f, axes=self.axes)
         return np.real(np.fft.ifftn(self.project_hat(fh), axes=self.axes))
 
     def material(self, f):
+        """Stress of every element, see apply_material."""
         return apply_material(f, self.E, self.nu)
 
     def operator(self, v):
@@ -337,7 +355,8 @@ class Problem:
         return self.project(self.material(v))
 
     def broadcast_macro(self, Emac):
-        """The homogeneous field holding the Mandel strain Emac on every element."""
+        """The homogeneous field holding the Mandel strain Emac on every element (the
+        macroscopic strain is the k = 0 mode, Sec. 2.3)."""
         Emac = np.asarray(Emac, dtype=np.float64)
         f = np.empty((self.m,) + self.E.shape)
         for q in range(self.nq):
@@ -348,7 +367,7 @@ class Problem:
     # -- the projected conjugate gradient (Sec. 2.1: gradient-based solver
     #    whose iterates stay compatible) ----------------------------------
     def solve(self, Emac, tol=1e-12, maxit=10000):
-        """Solve G C (E + eps~) = 0 for the compatible fluctuation eps~.
+        """Solve G C (E + eps~) = 0 (Eq. stat-mech-equi2) for the compatible fluctuation eps~.
 
         Start eps~ = 0, r = -A(E); plain CG with Euclidean inner products on
         the Mandel scalars; stop when ||r|| <= tol ||r_0||.  Returns
@@ -376,16 +395,19 @@ class Problem:
 
     # -- homogenisation ----------------------------------------------------
     def mean_stress(self, eps):
-        """Volume average of C eps over all N * n_q (equal-volume) elements."""
+        """Volume average of C eps over all N * n_q (equal-volume) elements: the
+        homogenised stress of Sec. 2.1."""
         sig = self.material(eps).reshape((self.nq, self.ns) + self.E.shape)
         return sig.mean(axis=tuple([0] + list(range(2, 2 + self.dim))))
 
     def energy_form(self, eps_a, eps_b):
-        """Volume average of eps_a : C : eps_b."""
+        """Volume average of eps_a : C : eps_b (the energy of the weak form,
+        Eq. stat-mech-equi-weak-form, evaluated on two solutions)."""
         return float(np.sum(eps_a * self.material(eps_b)) / (self.E.size * self.nq))
 
     def effective_tangent(self, Emacs, tol=1e-12, maxit=10000):
-        """C_eff from L = n_s linearly independent load cases (rows of Emacs).
+        """C_eff from L = n_s linearly independent load cases (rows of Emacs); each
+        load case prescribes the mean strain (Sec. 2.1).
 
         Column l of S is the mean stress of load case l; C_eff = S M^-1 with
         M[:, l] = E_l.  Returns (C_eff, fields, iteration counts).
@@ -403,7 +425,9 @@ class Problem:
 
     # -- adjoint gradient of J = W : C_eff w.r.t. the voxel moduli ---------
     def adjoint_gradient(self, W, tol=1e-12, maxit=10000):
-        """dJ/dE_v for J = sum_ab W_ab C_eff[a, b], C_eff from unit load cases.
+        """dJ/dE_v for J = sum_ab W_ab C_eff[a, b], C_eff from unit load cases.  The
+        paper has no gradient; this is the adjoint of the discrete equilibrium
+        G C eps = 0 (Eq. stat-mech-equi2).
 
         The adjoint of the mean-stress functional for row a is the projected
         problem with macroscopic strain e_a (the operator is self-adjoint), so

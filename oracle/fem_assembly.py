@@ -32,7 +32,8 @@ from .fe_projection import (array_shape, mandel_pairs, mandel_weight, n_strain,
 
 
 def element_vertices(dim):
-    """Vertex offsets (in voxel units) of the elements of one voxel."""
+    """Vertex offsets (in voxel units) of the elements of one voxel: the two triangles
+    of Sec. 2.6 in 2D, the six Kuhn tetrahedra (our reading of the 3D split) in 3D."""
     if dim == 2:
         return [np.array([[0, 0], [1, 0], [0, 1]]),
                 np.array([[1, 1], [0, 1], [1, 0]])]
@@ -47,7 +48,8 @@ def element_vertices(dim):
 
 
 def shape_function_gradients(X):
-    """Gradients of the linear shape functions of a simplex with vertices X.
+    """Gradients of the linear shape functions of a simplex with vertices X (the
+    linear elements of Sec. 2.6).
 
     N_i(x) = a_i + b_i . x with N_i(X_j) = delta_ij; returns b as (D+1, D)
     and the simplex volume.
@@ -60,7 +62,8 @@ def shape_function_gradients(X):
 
 
 def element_strain_matrix(grads):
-    """B_e: Mandel strain of element from its (D+1) nodal displacement vectors."""
+    """B_e: Mandel strain (Eq. small-strain) of an element from its (D+1) nodal
+    displacement vectors."""
     npts, D = grads.shape
     pairs = mandel_pairs(D)
     Be = np.zeros((len(pairs), npts * D))
@@ -75,7 +78,8 @@ def element_strain_matrix(grads):
 
 
 class AssembledFEM:
-    """Periodic linear-FE stiffness of a voxel grid with per-voxel moduli."""
+    """Periodic linear-FE stiffness of a voxel grid with per-voxel moduli: the
+    traditional finite-element problem that Sec. 2.6 says the FE projection reproduces."""
 
     def __init__(self, n, E, nu, length=None):
         self.n = tuple(int(v) for v in n)
@@ -105,6 +109,7 @@ class AssembledFEM:
         return p @ self.strides
 
     def _assemble(self):
+        """K = sum_e |e| B_e^T C_e B_e over all elements, periodic node numbering."""
         D, N = self.dim, self.N
         Ev = self.E.reshape(-1)  # voxel numbering = x fastest, matches idx rows
         rows, cols, vals = [], [], []
@@ -124,7 +129,7 @@ class AssembledFEM:
         self.ndof = ndof
 
     def load_vector(self, Emac):
-        """f = -sum_e |e| B_e^T C_e E."""
+        """f = -sum_e |e| B_e^T C_e E (the load of the prescribed mean strain, Sec. 2.1)."""
         Emac = np.asarray(Emac, dtype=np.float64)
         Ev = self.E.reshape(-1)
         f = np.zeros(self.ndof)
@@ -134,7 +139,8 @@ class AssembledFEM:
         return f
 
     def solve(self, Emac, direct=True, tol=1e-14):
-        """Nodal fluctuation u (node 0 pinned) for macroscopic strain Emac."""
+        """Nodal fluctuation u (node 0 pinned) for macroscopic strain Emac: K u = f,
+        the FE equilibrium of Sec. 2.6."""
         D = self.dim
         f = self.load_vector(Emac)
         free = np.arange(D, self.ndof)
@@ -161,7 +167,8 @@ class AssembledFEM:
         return np.concatenate(out, axis=0)
 
     def energy(self, Emac, u):
-        """sum_e |e| eps_e : C_e : eps_e (the minimised functional)."""
+        """sum_e |e| eps_e : C_e : eps_e (the minimised functional, the energy of
+        Eq. stat-mech-equi-weak-form)."""
         eps = self.element_strains(Emac, u).reshape((self.nq, self.ns, -1))
         Ev = self.E.reshape(-1)
         tot = 0.0
@@ -170,13 +177,14 @@ class AssembledFEM:
         return tot
 
     def mean_stress(self, eps):
-        """Volume average of C eps over all (equal-volume) elements."""
+        """Volume average of C eps over all (equal-volume) elements (Sec. 2.1)."""
         Ev = self.E.reshape(-1)
         e = eps.reshape((self.nq, self.ns, -1))
         sig = np.einsum("st,qtn->qsn", self.Cbar, e) * Ev[None, None, :]
         return sig.mean(axis=(0, 2))
 
     def effective_tangent(self, Emacs, direct=True):
+        """C_eff from n_s independent load cases, as Problem.effective_tangent (Sec. 2.1)."""
         Emacs = np.asarray(Emacs, dtype=np.float64)
         S = np.zeros((self.ns, len(Emacs)))
         fields = []
@@ -231,6 +239,7 @@ def finite_strain_fem(n, E, nu, Fmac, length=None, tol=1e-13, max_newton=50):
     I = np.eye(D)
 
     def element_F(u):
+        """F = I + grad u per element (Eq. def-grad) from the nodal displacement."""
         out = []
         for grads, vol, nodes in elems:
             U = u.reshape(N, D)[nodes]                           # (N, D+1, D): u_v,i
@@ -239,6 +248,7 @@ def finite_strain_fem(n, E, nu, Fmac, length=None, tol=1e-13, max_newton=50):
         return out
 
     def pk(F, e):
+        """St. Venant-Kirchhoff first Piola-Kirchhoff stress (as FiniteStrainProblem)."""
         C = np.einsum("eki,ekj->eij", F, F)
         Eg = 0.5 * (C - I[None])
         tr = np.trace(Eg, axis1=1, axis2=2)
@@ -246,6 +256,7 @@ def finite_strain_fem(n, E, nu, Fmac, length=None, tol=1e-13, max_newton=50):
         return S
 
     def assemble(u):
+        """Nodal force vector and dense tangent stiffness of the finite-strain problem."""
         g = np.zeros(ndof)
         K = np.zeros((ndof, ndof))
         for (grads, vol, nodes), F in zip(elems, element_F(u)):

@@ -44,7 +44,8 @@ from .fe_projection import array_shape, derivative_symbols, lame
 
 
 class FiniteStrainProblem:
-    """A periodic cell under finite strain (St. Venant-Kirchhoff per voxel)."""
+    """A periodic cell under finite strain (St. Venant-Kirchhoff per voxel; Sec. 3.1
+    names an isotropic finite-strain linear elastic law, this is our reading of it)."""
 
     def __init__(self, n, E, nu, length=None, derivative="fe"):
         self.n = tuple(int(v) for v in n)
@@ -64,7 +65,9 @@ class FiniteStrainProblem:
 
     # -- the projection -----------------------------------------------------
     def project(self, A):
-        """G applied to a gradient field A (n_q, D, D, *shape), real."""
+        """G applied to a gradient field A (n_q, D, D, *shape), real: the gradient
+        projection G_iabj = delta_ij g_ab of Eq. original-G with the element derivatives
+        of Eq. discrete_projection_op, row by row of F (Eq. def-grad)."""
         Ah = np.fft.fftn(A, axes=self.axes)
         t = np.einsum("qa...,qia...->i...", np.conj(self.g), Ah)      # B^H A per row i
         S = np.where(self.singular, 1.0, self.S)
@@ -74,7 +77,8 @@ class FiniteStrainProblem:
 
     # -- the law ------------------------------------------------------------
     def _pk2(self, F):
-        """Green-Lagrange strain and second Piola-Kirchhoff stress of every element."""
+        """Green-Lagrange strain and second Piola-Kirchhoff stress of every element
+        (St. Venant-Kirchhoff in the constants of Sec. 3.3, plane strain in 2D)."""
         D = self.dim
         C = np.einsum("qki...,qkj...->qij...", F, F)
         Eg = 0.5 * (C - np.eye(D)[None, :, :, *([None] * self.dim)])
@@ -85,12 +89,14 @@ class FiniteStrainProblem:
         return Eg, S
 
     def stress(self, F):
-        """First Piola-Kirchhoff stress P = F S of every element."""
+        """First Piola-Kirchhoff stress P = F S of every element (the stress of the
+        equilibrium G P(F) = 0, Eq. stat-mech-equi-FFT-homogenization)."""
         _, S = self._pk2(F)
         return np.einsum("qik...,qkj...->qij...", F, S)
 
     def tangent(self, F, dF):
-        """dP = dF S(F) + F (lambda tr(dE) I + 2 mu dE), dE = sym(F^T dF)."""
+        """dP = dF S(F) + F (lambda tr(dE) I + 2 mu dE), dE = sym(F^T dF): the
+        linearisation of stress() that Newton's method solves with."""
         _, S = self._pk2(F)
         FtdF = np.einsum("qki...,qkj...->qij...", F, dF)
         dE = 0.5 * (FtdF + np.swapaxes(FtdF, 1, 2))
@@ -102,12 +108,16 @@ class FiniteStrainProblem:
 
     # -- the solve ----------------------------------------------------------
     def broadcast(self, Fmac):
+        """The homogeneous deformation gradient Fmac on every element (the k = 0 mode
+        of F, Sec. 2.3)."""
         Fmac = np.asarray(Fmac, dtype=np.float64).reshape(self.dim, self.dim)
         return np.broadcast_to(Fmac[None, :, :, *([None] * self.dim)],
                                (self.nq, self.dim, self.dim) + self.E.shape).copy()
 
     def solve(self, Fmac, tol=1e-10, cg_tol=1e-12, max_newton=30, maxit=20000):
-        """Newton-projected-CG.  Stops when ||G P(F)|| <= tol ||G P(F_macro)||.
+        """Newton-projected-CG on G P(F) = 0 (Eq. stat-mech-equi-FFT-homogenization);
+        each correction is a projected CG solve of G K(F) dF = -G P(F).  Stops when
+        ||G P(F)|| <= tol ||G P(F_macro)||.
 
         Returns (F, Newton steps, total CG iterations, relative residual)."""
         F = self.broadcast(Fmac)
@@ -144,5 +154,6 @@ class FiniteStrainProblem:
         return F, steps, its, rn / r0
 
     def mean_stress(self, F):
-        """Volume average of P over all (equal-volume) elements, (D, D)."""
+        """Volume average of P over all (equal-volume) elements, (D, D): the
+        homogenised first Piola-Kirchhoff stress."""
         return self.stress(F).mean(axis=(0,) + self.axes)
