@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_error_strings(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert lib.rve_error_string(code)
     assert b"unknown" in lib.rve_error_string(42)
 

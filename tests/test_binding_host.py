@@ -84,3 +84,14 @@ def test_null_handle_is_an_argument_error():
     assert lib.rve_get_strain(None, 0, None, 0) == _rve.RVE_ERR_ARG
     assert isinstance(lib.rve_error_string(_rve.RVE_ERR_ARG), bytes)
     assert C.sizeof(_rve.rve_info) == 32
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the built library every entry point raises."""
+    saved = _rve._lib
+    _rve._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            _rve.load(str(tmp_path / "librve.so"))
+    finally:
+        _rve._lib = saved
