@@ -69,10 +69,12 @@ def _kron(mats):
     return out
 
 
-def _gradient_ops(derivative, n, delta=0.0):
-    """Dense d/dx_a, a < D, on x-fastest flattened grids (unit cell)."""
+def _gradient_ops(derivative, n, delta=0.0, length=None):
+    """Dense d/dx_a, a < D, on x-fastest flattened grids (cell edge lengths
+    ``length``, unit cell by default; voxel size h_a = L_a / n_a)."""
     D = len(n)
-    h = [1.0 / v for v in n]
+    length = length or (1.0,) * D
+    h = [L / v for L, v in zip(length, n)]
     ops = []
     for a in range(D):
         mats = []
@@ -112,6 +114,20 @@ def test_projection_is_least_squares_compatible_part(derivative, n):
     Br = _strain_operator(ops)
     P = Problem(n, np.ones(array_shape(n)), 0.3, derivative=derivative)
     f = np.random.default_rng(41).standard_normal((P.m,) + array_shape(n))
+    ref = Br @ np.linalg.lstsq(Br, f.reshape(-1), rcond=1e-10)[0]
+    assert np.abs(P.project(f).reshape(-1) - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("derivative,n,length", [("forward", (6, 5), (2.0, 0.5)), ("central", (5, 7), (0.4, 1.3)),
+                                                 ("lsq", (6, 4), (3.0, 1.0)), ("fourier", (5, 7), (1.5, 0.25)),
+                                                 ("lsq", (4, 4, 3), (1.0, 2.0, 0.5)),
+                                                 ("fourier", (3, 5, 3), (0.5, 1.0, 2.5))])
+def test_projection_on_anisotropic_voxels(derivative, n, length):
+    """The same least-squares characterisation with non-cubic voxels: the cell
+    lengths enter only through h_a in every stencil."""
+    Br = _strain_operator(_gradient_ops(derivative, n, length=length))
+    P = Problem(n, np.ones(array_shape(n)), 0.3, length=length, derivative=derivative)
+    f = np.random.default_rng(43).standard_normal((P.m,) + array_shape(n))
     ref = Br @ np.linalg.lstsq(Br, f.reshape(-1), rcond=1e-10)[0]
     assert np.abs(P.project(f).reshape(-1) - ref).max() < 1e-11 * np.abs(ref).max()
 

@@ -121,16 +121,19 @@ def test_rotated_load_rotates_mean_stress():
     assert np.abs(P.mean_stress(F2) - R @ P.mean_stress(F1)).max() < 1e-9 * np.abs(P.mean_stress(F1)).max()
 
 
-@pytest.mark.parametrize("n,Fm", [((6, 5), [[1.1, 0.05], [-0.02, 0.95]]),
-                                  ((3, 4, 3), [[1.06, 0.02, 0.0], [0.0, 0.97, 0.03], [-0.02, 0.0, 1.03]])])
-def test_equals_real_space_finite_strain_fem(n, Fm):
+@pytest.mark.parametrize("n,Fm,length", [((6, 5), [[1.1, 0.05], [-0.02, 0.95]], None),
+                                         ((6, 5), [[1.1, 0.05], [-0.02, 0.95]], (2.0, 0.6)),
+                                         ((3, 4, 3), [[1.06, 0.02, 0.0], [0.0, 0.97, 0.03], [-0.02, 0.0, 1.03]],
+                                          None)])
+def test_equals_real_space_finite_strain_fem(n, Fm, length):
     """O3 (projection, Fourier space) against a Newton solve of the assembled
-    periodic finite-strain FE problem in real space (O2's shape functions)."""
+    periodic finite-strain FE problem in real space (O2's shape functions),
+    on cubic and on non-cubic voxels."""
     from oracle.fem_assembly import finite_strain_fem
     E = np.exp(np.random.default_rng(56).standard_normal(array_shape(n)))
-    P = FiniteStrainProblem(n, E, 0.3)
+    P = FiniteStrainProblem(n, E, 0.3, length=length)
     F, _, _, _ = P.solve(np.array(Fm), tol=1e-13)
-    F_fem, P_fem, steps = finite_strain_fem(n, E, 0.3, Fm)
+    F_fem, P_fem, steps = finite_strain_fem(n, E, 0.3, Fm, length=length)
     assert steps >= 2
     assert np.abs(P.mean_stress(F) - P_fem).max() < 1e-11 * np.abs(P_fem).max()
     assert np.abs(F.reshape(F_fem.shape) - F_fem).max() < 1e-10

@@ -31,6 +31,25 @@ def test_projected_cg_equals_assembled_fem(n):
         assert np.abs(a - b).max() < 1e-11
 
 
+@pytest.mark.parametrize("n,length", [((6, 8), (2.0, 0.5)), ((5, 4), (0.3, 1.7)), ((4, 3, 5), (1.0, 3.0, 0.7))])
+def test_projected_cg_equals_assembled_fem_on_anisotropic_voxels(n, length):
+    """Cell lengths enter O1 only through h_a = L_a / n_a in the element symbols
+    (Appendix A grid) and O2 only through the vertex coordinates of its
+    elements; both must give the same solution on non-cubic voxels."""
+    E = _lognormal(n, 3)
+    P = Problem(n, E, 0.3, length=length)
+    I = np.eye(P.ns)
+    C1, f1, _ = P.effective_tangent(I, tol=1e-13)
+    fem = AssembledFEM(n, E, 0.3, length=length)
+    C2, f2 = fem.effective_tangent(I)
+    assert np.abs(C1 - C2).max() <= 1e-12 * np.abs(C2).max()
+    for a, b in zip(f1, f2):
+        assert np.abs(a - b).max() < 1e-11
+    # and the voxel shape matters: the unit-cell answer is different
+    C0, _, _ = Problem(n, E, 0.3).effective_tangent(I, tol=1e-13)
+    assert np.abs(C0 - C1).max() > 1e-3 * np.abs(C1).max()
+
+
 @pytest.mark.parametrize("n", [(3, 4), (2, 3, 2)])
 def test_fem_equals_dense_minimiser(n):
     E = _lognormal(n, 2)
