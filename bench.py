@@ -215,6 +215,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def hbm_fractions(mb, kt, lc_iters, steps, peak):
+    """Achieved HBM fraction of every timed CG-iteration kernel: its model bytes
+    per load-case iteration x the load-case iterations it served / its summed
+    CUDA-event time, over the peak (GB/s).  Kernels without time are left out."""
+    out = {}
+    for k, (ms, launches) in kt.items():
+        if k in mb and launches > 0 and ms > 0:
+            out[k] = mb[k] * lc_iters * steps / (ms * 1e-3) / 1e9 / peak
+    return out
+
+
 def host_cpu(cpuinfo=None):
     """CPU model and logical core count of this host (for the CPU baseline).
 
@@ -533,6 +544,7 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": measured_traffic(cfg_name, args.form, dom, dim), "kernel": dom,
                      "peak_source": peak_kind},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "kernels_hbm_frac": hbm_fractions(mb, kt, lc_iters, args.steps, peak),
         "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant"), r.schedule()[0])),
         "e2e": {"value": job_throughput(1.0, e2e_s, world), "unit": "solves/s", "h2d_bytes_per_step": int(E_host.nbytes + Em.nbytes),
                 "d2h_bytes_per_step": int(C_h.nbytes)},

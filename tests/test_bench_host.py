@@ -45,3 +45,13 @@ def test_host_cpu_description():
     assert bench.host_cpu(x86)["model"] == "Some CPU @ 3.0GHz"
     arm = "processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n"
     assert bench.host_cpu(arm)["model"].endswith("CPU part 0xd4f")
+
+
+def test_hbm_fractions():
+    mb = bench.model_bytes(2, (1024, 1024), 4, 1)
+    # pass A moving its model bytes for 100 load-case iterations in 10 ms at a 6000 GB/s peak
+    kt = {"pass_a": (10.0, 50), "pass_c": (0.0, 0), "residual": (1.0, 3), "pass_e": (5.0, 50)}
+    f = bench.hbm_fractions(mb, kt, 100.0, 1, 6000.0)
+    assert set(f) == {"pass_a", "pass_e"}               # untimed and non-model kernels left out
+    assert np.isclose(f["pass_a"], mb["pass_a"] * 100 / 10e-3 / 1e9 / 6000.0)
+    assert np.isclose(f["pass_e"] / f["pass_a"], (mb["pass_e"] / 5.0) / (mb["pass_a"] / 10.0))
