@@ -40,6 +40,41 @@ WORKLOADS = {
 }
 
 
+# Workloads of the widened rows: zero-stiffness voxels, a derivative plug-in,
+# finite strain and the adjoint gradient.  Same timing rules as the headline
+# workloads; each reports its own unit of work.
+EXTENSIONS = {
+    "porous1024": "zero-stiffness voxels: 1024^2 log-normal moduli with 25% void voxels, mixed, 3 load cases",
+    "fourier1024_fp64": "Fourier-derivative projection: the 1024^2 two-phase field, FP64, 3 load cases",
+    "finite1024_fp64": "finite strain (St. Venant-Kirchhoff): 1024^2 log-normal moduli, FP64, one F_macro",
+    "adjoint64": "adjoint gradient of C_1111: 64^3 log-normal moduli, mixed, 6 load cases + 1 adjoint solve",
+}
+
+
+def extension_inputs(name):
+    """Seeded inputs of an extension workload (grid, moduli, loads, precision)."""
+    import microstructures as ms
+    if name == "porous1024":
+        n = (1024, 1024)
+        return dict(n=n, E=ms.porous_lognormal(n, 0.25, seed=1009), nu=0.3, prec="mixed", tol=1e-10,
+                    Em=np.eye(3), unit="solves/s")
+    if name == "fourier1024_fp64":
+        cfg = ms.config_inputs("gauss1024")
+        return dict(n=cfg["n"], E=cfg["E"], nu=cfg["nu"], prec="fp64", tol=1e-10, Em=np.eye(3),
+                    derivative="fourier", unit="solves/s")
+    if name == "finite1024_fp64":
+        n = (1024, 1024)
+        return dict(n=n, E=ms.lognormal_field(n, 0.0, 1.0, seed=1010), nu=0.3, prec="fp64", tol=1e-10,
+                    Fm=np.array([[[1.05, 0.02], [0.0, 0.97]]]), unit="solves/s")
+    if name == "adjoint64":
+        cfg = ms.config_inputs("lognormal64")
+        W = np.zeros((6, 6))
+        W[0, 0] = 1.0
+        return dict(n=cfg["n"], E=cfg["E"], nu=cfg["nu"], prec="mixed", tol=1e-10, Em=np.eye(6), W=W,
+                    unit="gradients/s")
+    raise KeyError(name)
+
+
 def max_over_ranks(value, dist=None, device="cpu"):
     """The largest value over all ranks (the slowest rank sets the job time)."""
     if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
@@ -382,6 +417,87 @@ def run_batch(args, world, rank, local, dist):
         dist.destroy_process_group()
 
 
+def run_extension(args):
+    """One GPU, one handle: time whole solves (or solve + adjoint) of an
+    extension workload through the public API, inputs resident on the device."""
+    import torch
+    from paper_2105_03297_gb300 import RVE
+    from paper_2105_03297_gb300.build import build_library
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build_library()
+    x = extension_inputs(args.workload)
+    n, dim = x["n"], len(x["n"])
+    stream = torch.cuda.current_stream()
+    r = RVE(n, precision=x["prec"], stream=stream.cuda_stream)
+    if "derivative" in x:
+        r.set_derivative(x["derivative"])
+    if "Fm" in x:
+        r.set_kinematics("finite")
+    elif args.form != "stress":
+        r.set_operator_form(args.form)
+    E_dev = torch.from_numpy(np.ascontiguousarray(x["E"].reshape(-1))).cuda()
+    r.set_material(E_dev, x["nu"])
+
+    def step():
+        if "Fm" in x:
+            code, info = r.solve_finite(x["Fm"], rel_tol=x["tol"])
+            r.mean_piola()
+        else:
+            code, info = r.solve(x["Em"], rel_tol=x["tol"], max_iter=20000)
+            r.effective_tangent()
+            if "W" in x:
+                r.adjoint(x["W"], rel_tol=x["tol"], max_iter=20000)
+        return code, info
+
+    for _ in range(args.warmup):
+        step()
+    r.timing(True)
+    r.timing_read()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    codes, lc_iters = [], 0.0
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            code, info = step()
+            codes.append(code)
+            lc_iters += sum(i["iterations"] for i in info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    kt = r.timing_read()
+    r.timing(False)
+    r.close()
+    peak, peak_kind = peaks()
+    s = 4 if x["prec"] == "mixed" else 8
+    out = {
+        "metric": METRIC, "value": 1e3 * args.steps / ms_total, "unit": x["unit"], "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if x["prec"] == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": EXTENSIONS[args.workload], "grid": list(n),
+                   "precision": x["prec"], "rel_tol": x["tol"], "operator_form": args.form,
+                   "l2": "inputs larger than L2 (working set > 129 MB)"},
+        "status_codes": codes,
+        "cg_iterations_per_step": lc_iters / args.steps,
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "gpu_launches": int(sum(v[1] for v in kt.values())),
+        "clocks": clk.summary(),
+        "roofline": None,
+    }
+    if "Fm" not in x and "W" not in x and "derivative" not in x and args.form == "stress":
+        # small-strain FE stress form: the byte model of the headline workloads applies
+        mb = model_bytes(dim, n, s, 1)
+        fr = hbm_fractions(mb, kt, lc_iters, 1, peak)
+        out["kernels_hbm_frac"] = fr
+        if fr:
+            dom = max(fr, key=lambda k: kt[k][0])
+            out["roofline"] = {"bound": "hbm", "achieved": fr[dom] * peak, "peak": peak, "unit": "GB/s",
+                               "frac": fr[dom], "traffic": None, "kernel": dom, "peak_source": peak_kind}
+    print(json.dumps(out), flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -574,7 +690,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="gauss1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="gauss1024", choices=sorted(WORKLOADS) + sorted(EXTENSIONS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
                     help="force the tile variants of passes A and E, e.g. 0,0 (default: autotune)")
@@ -583,6 +699,13 @@ def main():
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the FP64 GPU solve and cuFFT timings (context figures)")
     args = ap.parse_args()
+    if args.workload in EXTENSIONS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle baseline is timed on the "
+                              "headline workloads only"}), flush=True)
+        elif int(os.environ.get("RANK", "0")) == 0:
+            run_extension(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

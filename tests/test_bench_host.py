@@ -55,3 +55,19 @@ def test_hbm_fractions():
     assert set(f) == {"pass_a", "pass_e"}               # untimed and non-model kernels left out
     assert np.isclose(f["pass_a"], mb["pass_a"] * 100 / 10e-3 / 1e9 / 6000.0)
     assert np.isclose(f["pass_e"] / f["pass_a"], (mb["pass_e"] / 5.0) / (mb["pass_a"] / 10.0))
+
+
+def test_extension_workloads_inputs():
+    for name in bench.EXTENSIONS:
+        x = bench.extension_inputs(name)
+        assert x["E"].shape == tuple(reversed(x["n"])) and np.all(x["E"] >= 0) and np.any(x["E"] > 0)
+        assert x["prec"] in ("mixed", "fp64")
+        # finite strain and the other derivatives run in FP64 only
+        if "Fm" in x or "derivative" in x:
+            assert x["prec"] == "fp64"
+        if "Fm" in x:
+            assert x["Fm"].shape == (1, len(x["n"]), len(x["n"]))
+        else:
+            assert x["Em"].shape == (3 if len(x["n"]) == 2 else 6,) * 2
+    assert (bench.extension_inputs("porous1024")["E"] == 0).mean() > 0.2
+    assert not set(bench.EXTENSIONS) & set(bench.WORKLOADS)
