@@ -1,0 +1,51 @@
+"""Randomised pins of the oracle (CPU): over random tiny grids (even and odd
+sizes, 2D and 3D), Poisson ratios, cell lengths and moduli, the projected CG
+(O1) equals the assembled real-space FEM (O2), the projection is an
+orthogonal projector, and C_eff lies between the Voigt and Reuss bounds.
+"""
+import numpy as np
+import pytest
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+from oracle.closed_forms import voigt_reuss  # noqa: E402
+from oracle.fe_projection import Problem, array_shape  # noqa: E402
+from oracle.fem_assembly import AssembledFEM  # noqa: E402
+
+grids = st.one_of(
+    st.tuples(st.integers(2, 7), st.integers(2, 7)),
+    st.tuples(st.integers(2, 4), st.integers(2, 4), st.integers(2, 4)),
+)
+
+
+@settings(max_examples=25, deadline=None)
+@given(n=grids, nu=st.floats(0.0, 0.45), seed=st.integers(0, 2**31 - 1), aniso=st.booleans())
+def test_o1_equals_o2(n, nu, seed, aniso):
+    rng = np.random.default_rng(seed)
+    E = np.exp(1.5 * rng.standard_normal(array_shape(n)))
+    length = tuple(rng.uniform(0.3, 3.0, len(n))) if aniso else None
+    P = Problem(n, E, nu, length=length)
+    I = np.eye(P.ns)
+    C1, _, _ = P.effective_tangent(I, tol=1e-13)
+    C2, _ = AssembledFEM(n, E, nu, length=length).effective_tangent(I)
+    assert np.abs(C1 - C2).max() <= 1e-10 * np.abs(C2).max()
+    V, R = voigt_reuss(E, nu, len(n))
+    Cs = 0.5 * (C1 + C1.T)
+    assert np.linalg.eigvalsh(V - Cs).min() > -1e-10 * np.abs(Cs).max()
+    assert np.linalg.eigvalsh(Cs - R).min() > -1e-10 * np.abs(Cs).max()
+
+
+@settings(max_examples=25, deadline=None)
+@given(n=grids, seed=st.integers(0, 2**31 - 1),
+       derivative=st.sampled_from(["fe", "fourier", "central", "forward", "lsq"]))
+def test_projection_is_an_orthogonal_projector(n, seed, derivative):
+    rng = np.random.default_rng(seed)
+    P = Problem(n, np.ones(array_shape(n)), 0.3, derivative=derivative)
+    f = rng.standard_normal((P.m,) + array_shape(n))
+    g = rng.standard_normal((P.m,) + array_shape(n))
+    Gf = P.project(f)
+    scale = np.abs(f).max()
+    assert np.abs(P.project(Gf) - Gf).max() < 1e-11 * scale                        # G G = G
+    assert abs(np.sum(Gf * g) - np.sum(f * P.project(g))) < 1e-10 * f.size * scale  # self-adjoint
+    assert np.sum(Gf * Gf) <= np.sum(f * f) * (1 + 1e-12)                           # a contraction
