@@ -49,3 +49,27 @@ def test_projection_is_an_orthogonal_projector(n, seed, derivative):
     assert np.abs(P.project(Gf) - Gf).max() < 1e-11 * scale                        # G G = G
     assert abs(np.sum(Gf * g) - np.sum(f * P.project(g))) < 1e-10 * f.size * scale  # self-adjoint
     assert np.sum(Gf * Gf) <= np.sum(f * f) * (1 + 1e-12)                           # a contraction
+
+
+finite_grids = st.one_of(
+    st.tuples(st.integers(2, 5), st.integers(2, 5)),
+    st.tuples(st.integers(2, 3), st.integers(2, 3), st.integers(2, 3)),
+)
+
+
+@settings(max_examples=15, deadline=None)
+@given(n=finite_grids, seed=st.integers(0, 2**31 - 1))
+def test_o3_equals_finite_strain_fem(n, seed):
+    """Finite strain: the gradient projection's Newton solve equals the real-space
+    finite-strain FE problem for random moduli and macroscopic deformations."""
+    from oracle.fem_assembly import finite_strain_fem
+    from oracle.finite_strain import FiniteStrainProblem
+    rng = np.random.default_rng(seed)
+    D = len(n)
+    E = np.exp(rng.standard_normal(array_shape(n)))
+    Fm = np.eye(D) + 0.08 * rng.standard_normal((D, D))
+    P = FiniteStrainProblem(n, E, 0.3)
+    F, _, _, _ = P.solve(Fm, tol=1e-13)
+    F_fem, P_fem, _ = finite_strain_fem(n, E, 0.3, Fm)
+    assert np.abs(P.mean_stress(F) - P_fem).max() < 1e-10 * np.abs(P_fem).max()
+    assert np.abs(F.reshape(F_fem.shape) - F_fem).max() < 1e-9
