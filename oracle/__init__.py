@@ -12,7 +12,7 @@ Two independent formulations of the same discrete problem:
   symbols of the linear-FE gradient stencils (Eq. genfourderiv), the
   small-strain projection G(k) = B (B^H B)^-1 B^H with G(0) = 0 (Eqs.
   discrete_projection_op, small-strain-eq2; the k = 0 rule of Sec. 2.3), the
-  DFT pair of Appendix A via numpy's FFT, and a plain projected conjugate
+  DFT pair of Appendix A (a direct matrix product per axis, or scipy's FFT), and a plain projected conjugate
   gradient (the gradient-based solver of Sec. 2.1).
 * ``fem_assembly`` (O2): the conforming periodic linear-FE problem it is
   equivalent to (Sec. 2.6), assembled element by element in real space from

@@ -1,8 +1,10 @@
 """O1: the finite-element compatibility projection and projected CG, in FP64.
 
-TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).  Plain, unblocked,
-unfused numpy; an FFT (``numpy.fft``) and small batched linear solves are the
-only library steps.
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).  Plain, unfused numpy;
+the DFT (a matrix product per axis, or ``scipy.fft``) and small batched
+linear solves are the only library steps.  The projection is applied one
+slab of wavevectors at a time (G(k) acts on each wavevector on its own), so
+that the symbols of a 256^3 grid never have to be held at once.
 
 Conventions (fixed once, used by every function):
 
@@ -22,11 +24,17 @@ Conventions (fixed once, used by every function):
   (a, b, c) of (x, y, z) in lexicographic order (the paper only calls the 3D
   generalisation straightforward; this split is our reading);
 * DFT: forward ``sum_r f(r) exp(-i k.r)``, inverse with ``1/N`` (Appendix A,
-  Eqs. discrete-fourier-trafo and inverse-discrete-fourier-trafo), which is
-  numpy's ``fftn``/``ifftn`` over the spatial axes;
+  Eqs. discrete-fourier-trafo and inverse-discrete-fourier-trafo).  Two
+  interchangeable evaluations: ``dft="direct"`` writes the sum out as one
+  matrix product per axis (the exponential of k.r factorises over the axes),
+  ``dft="fft"`` (default) calls ``scipy.fft.fftn``/``ifftn`` on all host
+  cores; ``tests/test_oracle_dft.py`` pins both to the definition (sign and
+  1/N) and to each other;
 * 2D material: isotropic small-strain Hooke's law in plane strain.
 
-Pinned by: ``tests/test_oracle_projection.py`` (G idempotent, Hermitian,
+Pinned by: ``tests/test_oracle_dft.py`` (both DFT evaluations equal the
+sums of Appendix A written out as loops on a small non-square grid, the
+projected solve is the same with either), ``tests/test_oracle_projection.py`` (G idempotent, Hermitian,
 rank D, G B = B, Hermitian symmetry in k, agreement with the literal
 Appendix-B index form and with the textbook Fourier projection),
 ``tests/test_oracle_solve.py`` (equality with the assembled FEM of O2,
@@ -37,8 +45,12 @@ differences, Euler identity).
 from __future__ import annotations
 
 import itertools
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
+import scipy.fft
+import scipy.linalg.blas
 
 SQRT2 = np.sqrt(2.0)
 
@@ -141,7 +153,7 @@ def apply_material(field, E, nu):
     nq = field.shape[0] // ns
     Cbar = stiffness_mandel(dim, 1.0, nu)
     f = field.reshape((nq, ns) + E.shape)
-    sig = np.einsum("st,qt...->qs...", Cbar, f) * E[None, None]
+    sig = np.moveaxis(np.tensordot(Cbar, f, axes=([1], [1])), 0, 1) * E[None, None]   # Cbar_st f_qt
     return sig.reshape(field.shape)
 
 
@@ -149,30 +161,49 @@ def apply_material(field, E, nu):
 # Fourier symbols of the element gradients (Eq. genfourderiv)
 # --------------------------------------------------------------------------
 
-def phase_factors(n):
+def wave_indices(n, rows=None, nkx=None):
+    """Integer wavevector components m_a per axis; ``rows`` (optional) keeps only
+    those indices of the slowest axis (z in 3D, y in 2D), ``nkx`` only the first
+    nkx indices of the x axis (the half spectrum of a real field)."""
+    idx = [np.arange(int(na)) for na in n]
+    if rows is not None:
+        idx[-1] = np.arange(int(n[-1]))[rows]
+    if nkx is not None:
+        idx[0] = np.arange(int(nkx))
+    return idx
+
+
+def symbol_shape(n, rows=None, nkx=None):
+    """Array shape of the wavevectors selected by ``rows`` and ``nkx`` (see wave_indices)."""
+    return tuple(len(i) for i in reversed(wave_indices(n, rows, nkx)))
+
+
+def phase_factors(n, rows=None, nkx=None):
     """exp(i k_a h_a) = exp(2 pi i m_a / n_a) on the full FFT grid, per axis: the wave
-    vectors of Eq. Fourier_wave_vectors for the forward DFT of Eq. discrete-fourier-trafo."""
+    vectors of Eq. Fourier_wave_vectors for the forward DFT of Eq. discrete-fourier-trafo.
+    ``rows`` and ``nkx`` select wavevectors (see wave_indices)."""
     D = len(n)
     out = []
-    for a, na in enumerate(n):
-        e = np.exp(2j * np.pi * np.arange(na) / na)
+    for a, (na, ma) in enumerate(zip(n, wave_indices(n, rows, nkx))):
+        e = np.exp(2j * np.pi * ma / na)
         sh = [1] * D
-        sh[D - 1 - a] = na
+        sh[D - 1 - a] = len(ma)
         out.append(e.reshape(sh))
     return out
 
 
-def element_gradient_symbols(n, length=None):
+def element_gradient_symbols(n, length=None, rows=None, nkx=None):
     """g[Theta][a](k): symbol of d/dx_a on element Theta.
 
     From Eq. genfourderiv with the stencils of the linear-FE elements: a node
     at +e_a relative to the voxel's lower corner contributes exp(i k_a h_a).
-    Returns an array of shape (n_q, D, *array_shape), complex128.
+    Returns an array of shape (n_q, D, *array_shape), complex128 (with ``rows``,
+    only those wavevectors of the slowest axis, see wave_indices).
     """
     D = len(n)
     h = voxel_size(n, length)
-    e = phase_factors(n)
-    shp = array_shape(n)
+    e = phase_factors(n, rows, nkx)
+    shp = symbol_shape(n, rows, nkx)
     one = np.ones(shp)
     if D == 2:
         # element 0 = nodes {00, 10, 01}: forward differences
@@ -196,24 +227,23 @@ def element_gradient_symbols(n, length=None):
 DERIVATIVES = ("fe", "fourier", "central", "forward", "lsq", "fourier2")
 
 
-def wrapped_angles(n):
+def wrapped_angles(n, rows=None, nkx=None):
     """theta_a = k_a h_a in (-pi, pi) per axis (broadcast shapes as phase_factors);
     the Nyquist index of an even axis gets theta = 0 (our reading of the
     ambiguity discussed in Sec. 2.7: the average of the two grid choices)."""
     D = len(n)
     out = []
-    for a, na in enumerate(n):
-        m = np.arange(na)
+    for a, (na, m) in enumerate(zip(n, wave_indices(n, rows, nkx))):
         w = np.where(m < (na + 1) // 2, m, m - na).astype(np.float64)
         if na % 2 == 0:
-            w[na // 2] = 0.0
+            w[m == na // 2] = 0.0
         sh = [1] * D
-        sh[D - 1 - a] = na
+        sh[D - 1 - a] = len(m)
         out.append((2.0 * np.pi * w / na).reshape(sh))
     return out
 
 
-def derivative_symbols(n, length=None, derivative="fe"):
+def derivative_symbols(n, length=None, derivative="fe", rows=None, nkx=None):
     """g[Theta][a](k) for the derivative ``derivative`` (shape (n_q, D, *array_shape)).
 
     fe:       the linear finite elements (``element_gradient_symbols``), n_q = 2 / 6;
@@ -223,22 +253,23 @@ def derivative_symbols(n, length=None, derivative="fe"):
               along a averaged over the voxel edges parallel to a);
     fourier:  i k_a = i theta_a / h_a (Eq. original-G's derivative);
     fourier2: Appendix C, two evaluation points (2D), i k_a exp(-+ i sum_b theta_b / 6).
+    ``rows`` and ``nkx`` select wavevectors (see wave_indices).
     """
     if derivative == "fe":
-        return element_gradient_symbols(n, length)
+        return element_gradient_symbols(n, length, rows, nkx)
     D = len(n)
     h = voxel_size(n, length)
     # phases with the exact values at theta = 0, pi/2, pi, 3pi/2, so that the
     # derivatives that vanish there (central differences, least squares) vanish
     # exactly rather than at the rounding level of sin(pi)
     e = []
-    for ea in phase_factors(n):
+    for ea in phase_factors(n, rows, nkx):
         ea = ea.copy()
         ea.real[np.abs(ea.real) < 1e-14] = 0.0
         ea.imag[np.abs(ea.imag) < 1e-14] = 0.0
         e.append(ea)
-    th = wrapped_angles(n)
-    shp = array_shape(n)
+    th = wrapped_angles(n, rows, nkx)
+    shp = symbol_shape(n, rows, nkx)
     one = np.ones(shp)
     if derivative == "forward":
         return np.array([[(e[a] - 1.0) / h[a] * one for a in range(D)]])
@@ -265,24 +296,32 @@ def derivative_symbols(n, length=None, derivative="fe"):
     raise ValueError(derivative)
 
 
-def strain_symbol(g):
-    """B(k): (*array_shape, m, D) complex, Fourier symbol of u -> sym(grad_Theta u),
-    the element strain of Eq. small-strain with the element derivatives g_Theta(k).
+def strain_symbol_components(g):
+    """B(k) stored component-major, shape (m, D, *array_shape): the Fourier symbol of
+    u -> sym(grad_Theta u), the element strain of Eq. small-strain with the element
+    derivatives g_Theta(k).
 
     Row Theta*n_s + s, column j is Mandel component s of sym(g_Theta (x) e_j).
     """
     nq, D = g.shape[0], g.shape[1]
     pairs = mandel_pairs(D)
     ns = len(pairs)
-    shp = g.shape[2:]
-    B = np.zeros(shp + (nq * ns, D), dtype=np.complex128)
+    B = np.zeros((nq * ns, D) + g.shape[2:], dtype=np.complex128)
     for q in range(nq):
         for s, (a, b) in enumerate(pairs):
             for j in range(D):
                 # sym(g (x) e_j)_{ab} = (g_a delta_bj + g_b delta_aj) / 2
-                val = 0.5 * ((g[q, a] if b == j else 0.0) + (g[q, b] if a == j else 0.0))
-                B[..., q * ns + s, j] = mandel_weight(a, b) * val
+                if b == j:
+                    B[q * ns + s, j] += 0.5 * mandel_weight(a, b) * g[q, a]
+                if a == j:
+                    B[q * ns + s, j] += 0.5 * mandel_weight(a, b) * g[q, b]
     return B
+
+
+def strain_symbol(g):
+    """B(k) as one m x D matrix per wavevector: shape (*array_shape, m, D) (see
+    strain_symbol_components)."""
+    return np.ascontiguousarray(np.moveaxis(strain_symbol_components(g), (0, 1), (-2, -1)))
 
 
 def projection_matrices(B):
@@ -299,11 +338,72 @@ def projection_matrices(B):
     return G
 
 
+# --------------------------------------------------------------------------
+# The DFT pair of Appendix A (Eqs. discrete-fourier-trafo and
+# inverse-discrete-fourier-trafo)
+# --------------------------------------------------------------------------
+
+def dft_direct(f, inverse=False):
+    """Forward ``F(k) = sum_r f(r) exp(-2 pi i sum_a k_a r_a / n_a)`` over every axis
+    of ``f`` (inverse: ``+`` sign and a factor 1/n_a per axis), evaluated as written.
+
+    exp(-2 pi i k.r) is a product of one factor per axis, so the D-dimensional
+    sum is D one-dimensional sums, each a product with the n_a x n_a matrix
+    W_a[k, r] = exp(-+2 pi i (k r mod n_a) / n_a)."""
+    out = np.asarray(f, dtype=np.complex128)
+    sign = 1.0 if inverse else -1.0
+    for ax in range(out.ndim):
+        na = out.shape[ax]
+        k = np.arange(na)
+        W = np.exp(sign * 2j * np.pi * (np.outer(k, k) % na) / na)
+        out = np.moveaxis(np.tensordot(W, out, axes=([1], [ax])), 0, ax)
+        if inverse:
+            out = out / na
+    return out
+
+
+def dft_fast(f, inverse=False):
+    """The same transform pair by scipy's FFT on all host cores."""
+    fn = scipy.fft.ifftn if inverse else scipy.fft.fftn
+    return fn(np.asarray(f), workers=os.cpu_count() or 1)
+
+
+def rdft_fast(f):
+    """The forward DFT of a real field at k_x = 0..n_x/2 only (scipy, all host cores):
+    for real f, F(-k) = conj F(k), so these hold every independent value."""
+    return scipy.fft.rfftn(np.asarray(f), workers=os.cpu_count() or 1)
+
+
+def irdft_fast(F, shape):
+    """The inverse DFT (with 1/N) of a spectrum with F(-k) = conj F(k), given at
+    k_x = 0..n_x/2 (see rdft_fast); returns the real field of ``shape``."""
+    return scipy.fft.irfftn(F, s=shape, workers=os.cpu_count() or 1)
+
+
+DFTS = ("direct", "fft")
+
+
+# --------------------------------------------------------------------------
+# Vector operations of the CG (library BLAS on whole fields)
+# --------------------------------------------------------------------------
+
+def inner(a, b):
+    """<a, b> = sum_i a_i b_i over every entry of two real fields."""
+    return float(np.vdot(a, b))
+
+
+def axpy(alpha, x, y):
+    """y += alpha * x in place (y a C-contiguous float64 field)."""
+    assert y.flags.c_contiguous and y.dtype == np.float64
+    out = scipy.linalg.blas.daxpy(np.ascontiguousarray(x).reshape(-1), y.reshape(-1), a=alpha)
+    assert np.shares_memory(out, y)
+
+
 class Problem:
     """A periodic RVE (Sec. 2.1): grid of Appendix A, cell lengths, per-voxel moduli
     and Poisson ratio, with the discrete derivative that defines B(k) (Sec. 2.3)."""
 
-    def __init__(self, n, E, nu, length=None, derivative="fe"):
+    def __init__(self, n, E, nu, length=None, derivative="fe", dft="fft"):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         self.E = np.asarray(E, dtype=np.float64)
@@ -311,40 +411,98 @@ class Problem:
         self.nu = float(nu)
         self.length = length
         self.derivative = derivative
+        assert dft in DFTS
+        self.dft = dft
         self.ns = n_strain(self.dim)
-        self.g = derivative_symbols(self.n, length, derivative)
-        self.nq = self.g.shape[0]
+        self.nq = derivative_symbols((2,) * self.dim, None, derivative).shape[0]
         self.m = self.ns * self.nq
-        self.B = strain_symbol(self.g)  # (*shape, m, D)
-        BH = np.conj(np.swapaxes(self.B, -1, -2))
-        M = BH @ self.B
-        # G = 0 where B vanishes: k = 0 (Sec. 2.3) and, for derivatives that
-        # vanish at other wavevectors (central differences, least squares, the
-        # zeroed Nyquist of the Fourier derivative), those wavevectors too
-        self.singular = np.all(np.abs(self.B) == 0.0, axis=(-2, -1))
-        self.singular[(0,) * self.dim] = True
-        M[self.singular] = np.eye(self.dim)
-        self.BHB = M  # B^H B with the singular blocks replaced by I (never used there)
-        self.axes = tuple(range(1, self.dim + 1))
+        self.axes = tuple(range(1, self.dim + 1))   # spatial axes of an (m, *shape) field
+        self.slab_entries = 1 << 23   # entries of B per slab of wavevectors in project_hat
+        self._full = None
+
+    def symbols(self, rows=None, nkx=None):
+        """(g, B, B^H B, singular) at the wavevectors selected by ``rows`` and ``nkx``
+        (see wave_indices), component-major: element derivatives g (n_q, D, *shape),
+        B(k) (m, D, *shape), B^H B (D, D, *shape) with identity blocks where G is
+        zero, and that mask (*shape).
+
+        G = 0 where B vanishes: k = 0 (Sec. 2.3) and, for derivatives that vanish
+        at other wavevectors (central differences, least squares, the zeroed
+        Nyquist of the Fourier derivative), those wavevectors too."""
+        g = derivative_symbols(self.n, self.length, self.derivative, rows, nkx)
+        B = strain_symbol_components(g)
+        M = np.einsum("cj...,ck...->jk...", np.conj(B), B)
+        singular = np.all(B == 0.0, axis=(0, 1))
+        hit = np.flatnonzero(wave_indices(self.n, rows)[-1] == 0)     # the k = 0 wavevector
+        if hit.size:
+            singular[(int(hit[0]),) + (0,) * (self.dim - 1)] = True
+        for j in range(self.dim):
+            for k in range(self.dim):
+                M[j, k][singular] = 1.0 if j == k else 0.0
+        return g, B, M, singular
+
+    def _all_symbols(self):
+        if self._full is None:
+            self._full = self.symbols()
+        return self._full
+
+    # whole-grid symbols as one matrix per wavevector, for the pins on small grids
+    g = property(lambda self: self._all_symbols()[0])
+    B = property(lambda self: np.ascontiguousarray(np.moveaxis(self._all_symbols()[1], (0, 1), (-2, -1))))
+    BHB = property(lambda self: np.ascontiguousarray(np.moveaxis(self._all_symbols()[2], (0, 1), (-2, -1))))
+    singular = property(lambda self: self._all_symbols()[3])
 
     # -- the projection, applied in the factored form B (B^H B)^-1 B^H ----
     def project_hat(self, fh):
-        """Apply G(k) to a spectrum ``fh`` of shape (m, *shape); G(0) = 0 (Sec. 2.3).
+        """Apply G(k) to a spectrum ``fh`` of shape (m, *shape), in place; G(0) = 0
+        (Sec. 2.3).  ``fh`` holds either every wavevector or (real fields) only
+        k_x = 0..n_x/2, as its last axis says.
 
         G = B (B^H B)^-1 B^H is the small-strain projection of Appendix B
-        (Eqs. small-strain-eq2, small-strain-chi) in matrix form."""
-        x = np.moveaxis(fh, 0, -1)[..., None]            # (*shape, m, 1)
-        t = np.conj(np.swapaxes(self.B, -1, -2)) @ x      # B^H f
-        u = np.linalg.solve(self.BHB, t)                  # (B^H B)^-1 B^H f
-        y = (self.B @ u)[..., 0]                          # B (...)
-        y[self.singular] = 0.0
-        return np.moveaxis(y, -1, 0)
+        (Eqs. small-strain-eq2, small-strain-chi) in matrix form.  G(k) acts on
+        each wavevector alone; the wavevectors are taken a slab of the slowest
+        axis at a time (so that B is never held for the whole grid), and the
+        slabs, which share nothing, on all host cores at once."""
+        nkx = fh.shape[-1]
+        assert nkx in (self.n[0], self.n[0] // 2 + 1)
+        per_row = int(np.prod(fh.shape[2:])) * self.m * self.dim
+        step = max(1, self.slab_entries // per_row)
+
+        def one_slab(r0):
+            rows = slice(r0, min(r0 + step, self.n[-1]))
+            _, B, M, singular = self.symbols(rows, nkx)
+            t = np.einsum("cj...,c...->j...", np.conj(B), fh[:, rows])      # B^H f
+            u = np.linalg.solve(np.moveaxis(M, (0, 1), (-2, -1)),
+                                np.moveaxis(t, 0, -1)[..., None])[..., 0]  # (B^H B)^-1 B^H f
+            y = np.einsum("cj...,...j->c...", B, u)                        # B (...)
+            y[:, singular] = 0.0
+            fh[:, rows] = y
+
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+            list(ex.map(one_slab, range(0, self.n[-1], step)))
+        return fh
 
     def project(self, f):
-        """Real-space projection F^-1[ G(k) F[f](k) ] of an (m, *shape) field, with the
-        DFT pair of Eqs. discrete-fourier-trafo and inverse-discrete-fourier-trafo."""
-        fh = np.fft.fftn(f, axes=self.axes)
-        return np.real(np.fft.ifftn(self.project_hat(fh), axes=self.axes))
+        """Real-space projection F^-1[ G(k) F[f](k) ] of an (m, *shape) real field, with
+        the DFT pair of Eqs. discrete-fourier-trafo and inverse-discrete-fourier-trafo
+        (one component at a time).  ``dft="direct"`` transforms every wavevector;
+        ``dft="fft"`` keeps k_x = 0..n_x/2, which hold every independent value of the
+        spectrum of a real field: G(-k) = conj G(k), so the projected spectrum keeps
+        F(-k) = conj F(k) and its inverse is the same real field."""
+        shape = f.shape[1:]
+        if self.dft == "direct":
+            fh = np.empty(f.shape, dtype=np.complex128)
+            for c in range(f.shape[0]):
+                fh[c] = dft_direct(f[c])
+        else:
+            fh = np.empty(f.shape[:-1] + (self.n[0] // 2 + 1,), dtype=np.complex128)
+            for c in range(f.shape[0]):
+                fh[c] = rdft_fast(f[c])
+        self.project_hat(fh)
+        out = np.empty(f.shape)
+        for c in range(f.shape[0]):
+            out[c] = np.real(dft_direct(fh[c], inverse=True)) if self.dft == "direct" else irdft_fast(fh[c], shape)
+        return out
 
     def material(self, f):
         """Stress of every element, see apply_material."""
@@ -366,32 +524,48 @@ class Problem:
 
     # -- the projected conjugate gradient (Sec. 2.1: gradient-based solver
     #    whose iterates stay compatible) ----------------------------------
-    def solve(self, Emac, tol=1e-12, maxit=10000):
-        """Solve G C (E + eps~) = 0 (Eq. stat-mech-equi2) for the compatible fluctuation eps~.
+    def cg(self, Emac):
+        """The projected CG for G C (E + eps~) = 0 (Eq. stat-mech-equi2), one
+        iteration per step of the generator.
 
-        Start eps~ = 0, r = -A(E); plain CG with Euclidean inner products on
-        the Mandel scalars; stop when ||r|| <= tol ||r_0||.  Returns
-        (eps_total, iterations, relative residual).
-        """
-        Ef = self.broadcast_macro(Emac)
-        x = np.zeros_like(Ef)
-        r = -self.operator(Ef)
-        rr0 = float(np.sum(r * r))
-        if rr0 == 0.0:
-            return Ef + x, 0, 0.0
-        p = r.copy()
+        Start eps~ = 0, r = -A(E), p = r; each iteration: q = A(p),
+        alpha = <r, r> / <p, q>, eps~ += alpha p, r -= alpha q,
+        beta = <r', r'> / <r, r>, p = r' + beta p.  <., .> is the plain sum over
+        every Mandel scalar of every element.  Yields (eps~, <r, r>, <r0, r0>)
+        before the first iteration and after each one."""
+        x = np.zeros((self.m,) + self.E.shape)
+        r = -self.operator(self.broadcast_macro(Emac))
+        rr0 = inner(r, r)
         rr = rr0
-        it = 0
-        while it < maxit and rr > tol * tol * rr0:
+        yield x, rr, rr0
+        if rr0 == 0.0:
+            return
+        p = r.copy()
+        while True:
             q = self.operator(p)
-            alpha = rr / float(np.sum(p * q))
-            x += alpha * p
-            r -= alpha * q
-            rr_new = float(np.sum(r * r))
-            p = r + (rr_new / rr) * p
+            alpha = rr / inner(p, q)
+            axpy(alpha, p, x)        # x += alpha p
+            axpy(-alpha, q, r)       # r -= alpha q
+            del q
+            rr_new = inner(r, r)
+            p *= rr_new / rr         # p = r + beta p
+            axpy(1.0, r, p)
             rr = rr_new
+            yield x, rr, rr0
+
+    def solve(self, Emac, tol=1e-12, maxit=10000):
+        """Solve G C (E + eps~) = 0 (Eq. stat-mech-equi2) for the compatible fluctuation
+        eps~ by the projected CG (see cg); stop when ||r|| <= tol ||r_0|| (at once
+        when r_0 = 0, a homogeneous cell).  Returns (eps_total, iterations,
+        relative residual)."""
+        it = -1
+        for x, rr, rr0 in self.cg(Emac):
             it += 1
-        return Ef + x, it, np.sqrt(rr / rr0)
+            if rr0 == 0.0 or it >= maxit or rr <= tol * tol * rr0:
+                break
+        rel = 0.0 if rr0 == 0.0 else np.sqrt(rr / rr0)
+        x += self.broadcast_macro(Emac)
+        return x, it, rel
 
     # -- homogenisation ----------------------------------------------------
     def mean_stress(self, eps):

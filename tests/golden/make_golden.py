@@ -21,6 +21,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 TOL = 1e-12
+SOURCE = "oracle.fe_projection.Problem (O1), FP64, scipy FFT of the real fields"
 
 
 def _run(name):
@@ -50,7 +51,7 @@ def _run(name):
         P = Problem(cfg["n"], cfg["E"], cfg["nu"])
         eps, it, res = P.solve(np.eye(6)[l], tol=TOL)
         out = dict(name=f"spheres128 load case {l}", n=list(cfg["n"]), nu=cfg["nu"], tol=TOL,
-                   source="oracle.fe_projection.Problem (O1), FP64, numpy FFT",
+                   source=SOURCE,
                    mean_stress=P.mean_stress(eps).tolist(), iterations=it, rel_residual=float(res),
                    seconds=time.time() - t0)
         with open(os.path.join(HERE, f"spheres128_lc{l}.json"), "w") as f:
@@ -61,7 +62,7 @@ def _run(name):
     t0 = time.time()
     P = Problem(cfg["n"], cfg["E"], cfg["nu"])
     out = dict(name=name, n=list(cfg["n"]), nu=cfg["nu"], tol=TOL,
-               source="oracle.fe_projection.Problem (O1), FP64, numpy FFT")
+               source=SOURCE)
     I = np.eye(P.ns)
     if name == "lognormal64":
         W = np.zeros((P.ns, P.ns)); W[0, 0] = 1.0
