@@ -1,4 +1,5 @@
 """Host logic of bench.py (CPU): the byte models and the stored-traffic lookup."""
+import json
 import os
 
 import numpy as np
@@ -21,21 +22,42 @@ def test_byte_models():
     assert sum(nod.values()) < 0.2 * sum(bench.model_bytes(3, (64, 64, 64), 4, 1).values())
 
 
-def test_traffic_rows_follow_the_kernel_hash():
+def test_traffic_rows_follow_the_kernel_hash(tmp_path):
     h = bench.kernel_source_hash()
     assert len(h) == 16 and all(c in "0123456789abcdef" for c in h)
-    path = os.path.join(bench.ROOT, "profiles", "traffic.md")
-    rows = [[c.strip() for c in line.strip().strip("|").split("|")] for line in open(path)
-            if line.startswith("| ") and not line.startswith("| workload")]
+    rows = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["entries"]
     assert rows
-    for w, form, kernel, b, hh, _note in rows:
-        kind, dim = kernel.rsplit("_", 1)
-        got = bench.measured_traffic(w, form, kind, int(dim[0]))
-        if hh == h:
-            assert np.isclose(got, float(b))
+    for e in rows:
+        kind, dim = e["kernel"].rsplit("_", 1)
+        got = bench.measured_traffic(e["workload"], e["form"], kind, int(dim[0]))
+        if e["source_hash"] == h:
+            assert np.isclose(got, e["bytes_per_launch"])
         else:
             assert got is None
     assert bench.measured_traffic("gauss1024", "stress", "no_such_pass", 2) is None
+    # an entry counts only under the hash it was taken with
+    p = tmp_path / "t.json"
+    ent = {"workload": "w", "form": "stress", "kernel": "pass_a_3d", "bytes_per_launch": 5.0}
+    p.write_text(json.dumps({"entries": [dict(ent, source_hash=h)]}))
+    assert bench.measured_traffic("w", "stress", "pass_a", 3, path=str(p)) == 5.0
+    p.write_text(json.dumps({"entries": [dict(ent, source_hash="0" * 16)]}))
+    assert bench.measured_traffic("w", "stress", "pass_a", 3, path=str(p)) is None
+
+
+def test_scope_model_bytes():
+    # 256^3, FP32 fields and spectra: (8 * 4 + 8 * 4) * 36 * N + 4 N = 38.7 GB per CG iteration
+    N = 256 ** 3
+    assert bench.scope_model_bytes(3, (256,) * 3, 4, 4, 4) == (64 * 36 + 4) * N
+    assert abs(bench.scope_model_bytes(3, (256,) * 3, 4, 4, 4) / 1e9 - 38.72) < 0.01
+    assert bench.scope_model_bytes(2, (1024, 1024), 8, 8, 8) == (8 * 8 + 4 * 8) * 6 * 1024 ** 2 + 8 * 1024 ** 2
+
+
+def test_oracle_error_uses_the_stored_result():
+    d = bench.golden("disc32")
+    C = np.array(d["C_eff"])
+    e = bench.oracle_error("disc32", C=C * (1 + 1e-12))
+    assert e["value"] < 2e-12 and "tangent" in e["quantity"]
+    assert bench.oracle_error("no_such_workload", C=C) is None
 
 
 def test_host_cpu_description():
