@@ -8,6 +8,8 @@ oracle's projected CG (O1) on the full grid to a relative residual of
 iteration counts.  ``disc32`` is also solved by the assembled FEM (O2) and
 both results are stored.  ``lognormal64`` additionally stores the oracle's
 adjoint gradient of J = C_1111 at 16 seeded voxels and its Euler sum.
+``batch4`` stores the tangents of the first RVE of each side (64, 128, 256,
+512) of the 64-RVE uneven batch.
 ``spheres128`` is solved one load case per process (``spheres128:<l>``, each
 writes ``spheres128_lc<l>.json``); ``spheres128:merge`` assembles
 ``spheres128.json`` from the six parts.  Nothing here calls the CUDA path.
@@ -55,6 +57,26 @@ def _run(name):
                    mean_stress=P.mean_stress(eps).tolist(), iterations=it, rel_residual=float(res),
                    seconds=time.time() - t0)
         with open(os.path.join(HERE, f"spheres128_lc{l}.json"), "w") as f:
+            json.dump(out, f, indent=1)
+        return name
+
+    if name == "batch4":
+        # the first RVE of each side (64, 128, 256, 512) of the 64-RVE uneven
+        # batch, three unit load cases each
+        batch = ms.uneven_batch_2d(64, seed=1004)
+        picks = {}
+        for i, (n, _) in enumerate(batch):
+            picks.setdefault(n[0], i)
+        t0 = time.time()
+        rves = []
+        for side in sorted(picks):
+            i = picks[side]
+            n, E = batch[i]
+            C, _, its = Problem(n, E, 0.3).effective_tangent(np.eye(3), tol=TOL)
+            rves.append(dict(index=i, n=list(n), C_eff=C.tolist(), iterations=its))
+        out = dict(name=name, recipe="microstructures.uneven_batch_2d(64, seed=1004)", nu=0.3, tol=TOL,
+                   source=SOURCE, rves=rves, seconds=time.time() - t0)
+        with open(os.path.join(HERE, name + ".json"), "w") as f:
             json.dump(out, f, indent=1)
         return name
 
