@@ -153,7 +153,10 @@ def apply_material(field, E, nu):
     nq = field.shape[0] // ns
     Cbar = stiffness_mandel(dim, 1.0, nu)
     f = field.reshape((nq, ns) + E.shape)
-    sig = np.moveaxis(np.tensordot(Cbar, f, axes=([1], [1])), 0, 1) * E[None, None]   # Cbar_st f_qt
+    if field.size < (1 << 20):
+        sig = np.einsum("st,qt...->qs...", Cbar, f) * E[None, None]
+    else:
+        sig = np.moveaxis(np.tensordot(Cbar, f, axes=([1], [1])), 0, 1) * E[None, None]   # Cbar_st f_qt
     return sig.reshape(field.shape)
 
 
@@ -362,22 +365,31 @@ def dft_direct(f, inverse=False):
     return out
 
 
-def dft_fast(f, inverse=False):
-    """The same transform pair by scipy's FFT on all host cores."""
+def _workers(f):
+    """Host threads for one transform: all cores for large arrays, one for small
+    ones (where starting threads costs more than it saves)."""
+    return (os.cpu_count() or 1) if np.size(f) >= (1 << 18) else 1
+
+
+def dft_fast(f, inverse=False, axes=None):
+    """The same transform pair by scipy's FFT on all host cores (over ``axes``,
+    default all)."""
     fn = scipy.fft.ifftn if inverse else scipy.fft.fftn
-    return fn(np.asarray(f), workers=os.cpu_count() or 1)
+    return fn(np.asarray(f), axes=axes, workers=_workers(f))
 
 
-def rdft_fast(f):
-    """The forward DFT of a real field at k_x = 0..n_x/2 only (scipy, all host cores):
-    for real f, F(-k) = conj F(k), so these hold every independent value."""
-    return scipy.fft.rfftn(np.asarray(f), workers=os.cpu_count() or 1)
+def rdft_fast(f, axes=None):
+    """The forward DFT of a real field at k_x = 0..n_x/2 only (scipy, all host cores;
+    x is the last of ``axes``): for real f, F(-k) = conj F(k), so these hold every
+    independent value."""
+    return scipy.fft.rfftn(np.asarray(f), axes=axes, workers=_workers(f))
 
 
-def irdft_fast(F, shape):
+def irdft_fast(F, shape, axes=None):
     """The inverse DFT (with 1/N) of a spectrum with F(-k) = conj F(k), given at
-    k_x = 0..n_x/2 (see rdft_fast); returns the real field of ``shape``."""
-    return scipy.fft.irfftn(F, s=shape, workers=os.cpu_count() or 1)
+    k_x = 0..n_x/2 (see rdft_fast); returns the real field with spatial shape
+    ``shape``."""
+    return scipy.fft.irfftn(F, s=shape, axes=axes, workers=_workers(F))
 
 
 DFTS = ("direct", "fft")
@@ -387,14 +399,24 @@ DFTS = ("direct", "fft")
 # Vector operations of the CG (library BLAS on whole fields)
 # --------------------------------------------------------------------------
 
+# Fields at least this large use the (multi-threaded) BLAS routines; smaller
+# ones plain numpy, where starting the BLAS threads would cost more.
+BLAS_MIN = 1 << 20
+
+
 def inner(a, b):
     """<a, b> = sum_i a_i b_i over every entry of two real fields."""
+    if a.size < BLAS_MIN:
+        return float(np.sum(a * b))
     return float(np.vdot(a, b))
 
 
 def axpy(alpha, x, y):
     """y += alpha * x in place (y a C-contiguous float64 field)."""
     assert y.flags.c_contiguous and y.dtype == np.float64
+    if y.size < BLAS_MIN:
+        y += alpha * x
+        return
     out = scipy.linalg.blas.daxpy(np.ascontiguousarray(x).reshape(-1), y.reshape(-1), a=alpha)
     assert np.shares_memory(out, y)
 
@@ -418,7 +440,9 @@ class Problem:
         self.m = self.ns * self.nq
         self.axes = tuple(range(1, self.dim + 1))   # spatial axes of an (m, *shape) field
         self.slab_entries = 1 << 23   # entries of B per slab of wavevectors in project_hat
+        self.symbol_cache_bytes = 2 << 30   # keep every slab's symbols when they fit in this
         self._full = None
+        self._slabs = {}
 
     def symbols(self, rows=None, nkx=None):
         """(g, B, B^H B, singular) at the wavevectors selected by ``rows`` and ``nkx``
@@ -461,16 +485,25 @@ class Problem:
         G = B (B^H B)^-1 B^H is the small-strain projection of Appendix B
         (Eqs. small-strain-eq2, small-strain-chi) in matrix form.  G(k) acts on
         each wavevector alone; the wavevectors are taken a slab of the slowest
-        axis at a time (so that B is never held for the whole grid), and the
-        slabs, which share nothing, on all host cores at once."""
+        axis at a time (so that B need not be held for the whole grid; it is kept
+        between calls only when it is small), and the slabs, which share
+        nothing, on all host cores at once."""
         nkx = fh.shape[-1]
         assert nkx in (self.n[0], self.n[0] // 2 + 1)
         per_row = int(np.prod(fh.shape[2:])) * self.m * self.dim
         step = max(1, self.slab_entries // per_row)
 
+        keep = per_row * self.n[-1] * 16 <= self.symbol_cache_bytes
+
         def one_slab(r0):
             rows = slice(r0, min(r0 + step, self.n[-1]))
-            _, B, M, singular = self.symbols(rows, nkx)
+            key = (r0, step, nkx)
+            if key in self._slabs:
+                B, M, singular = self._slabs[key]
+            else:
+                _, B, M, singular = self.symbols(rows, nkx)
+                if keep:
+                    self._slabs[key] = (B, M, singular)
             t = np.einsum("cj...,c...->j...", np.conj(B), fh[:, rows])      # B^H f
             u = np.linalg.solve(np.moveaxis(M, (0, 1), (-2, -1)),
                                 np.moveaxis(t, 0, -1)[..., None])[..., 0]  # (B^H B)^-1 B^H f
@@ -478,8 +511,12 @@ class Problem:
             y[:, singular] = 0.0
             fh[:, rows] = y
 
-        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-            list(ex.map(one_slab, range(0, self.n[-1], step)))
+        starts = range(0, self.n[-1], step)
+        if len(starts) == 1:
+            one_slab(0)
+        else:
+            with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+                list(ex.map(one_slab, starts))
         return fh
 
     def project(self, f):
@@ -494,14 +531,22 @@ class Problem:
             fh = np.empty(f.shape, dtype=np.complex128)
             for c in range(f.shape[0]):
                 fh[c] = dft_direct(f[c])
-        else:
-            fh = np.empty(f.shape[:-1] + (self.n[0] // 2 + 1,), dtype=np.complex128)
+            self.project_hat(fh)
+            out = np.empty(f.shape)
             for c in range(f.shape[0]):
-                fh[c] = rdft_fast(f[c])
+                out[c] = np.real(dft_direct(fh[c], inverse=True))
+            return out
+        if f.size < (1 << 24):          # small fields: all components in one call
+            fh = rdft_fast(f, axes=self.axes)
+            self.project_hat(fh)
+            return irdft_fast(fh, shape, axes=self.axes)
+        fh = np.empty(f.shape[:-1] + (self.n[0] // 2 + 1,), dtype=np.complex128)
+        for c in range(f.shape[0]):
+            fh[c] = rdft_fast(f[c])
         self.project_hat(fh)
         out = np.empty(f.shape)
         for c in range(f.shape[0]):
-            out[c] = np.real(dft_direct(fh[c], inverse=True)) if self.dft == "direct" else irdft_fast(fh[c], shape)
+            out[c] = irdft_fast(fh[c], shape)
         return out
 
     def material(self, f):
