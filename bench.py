@@ -774,7 +774,9 @@ def run_gpu(args):
                                         "spectrum streams; all passes of one CG iteration, CUDA-event times"},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernels_hbm_frac": hbm_fractions(mb, kt, lc_iters, args.steps, peak),
-        "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant"), r.schedule()[0])),
+        "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant", "pass_c_fft_split", "pass_bd_fft_split"),
+                             r.schedule()[0])),
+        "schedule_candidate_ms": r.schedule()[1],
         "e2e": {"value": job_throughput(1.0, e2e_s, world), "unit": "solves/s", "h2d_bytes_per_step": int(E_host.nbytes + Em.nbytes),
                 "d2h_bytes_per_step": int(C_h.nbytes)},
         "gpu_launches": launches,
@@ -806,7 +808,8 @@ def main():
     ap.add_argument("--workload", default="lognormal256", choices=sorted(WORKLOADS) + sorted(EXTENSIONS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
-                    help="force the tile variants of passes A and E, e.g. 0,0 (default: autotune)")
+                    help="force the schedule: pass A, pass E tile variants [, pass C, B/D FFT splits], "
+                         "e.g. 0,0 or 3,0,0,0 (default: autotune)")
     ap.add_argument("--form", default="stress", choices=["stress", "factored", "nodal"],
                     help="order of the operator inside CG (same operator; see include/rve.h)")
     ap.add_argument("--no-comparisons", action="store_true",

@@ -42,6 +42,12 @@
  *    the legacy default stream), and calls return when their results are
  *    ready (host or device).  A handle must not be used by two host threads
  *    at once.  The CG iterations run as CUDA graphs of 8 iterations.
+ *  - Devices: a handle (and a batch) lives on the device that was current at
+ *    rve_create (rve_batch_create).  Every call makes that device current for
+ *    its duration and restores the caller's current device before it returns,
+ *    so handles on several devices can be used from one host thread.  Kernel
+ *    attributes are set once per device.  After cudaDeviceReset on a device,
+ *    destroy its handles; they are not usable again.
  *
  * Errors: every function returns RVE_OK (0) or a negative code; the text of a
  * code is rve_error_string(code).  After RVE_ERR_CUDA the handle should be
@@ -163,12 +169,24 @@ int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags);
  * material step is skipped and q = G * p (the bare projection). */
 int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int ptr_flags);
 
-/* Schedule of the FFT passes (tile shapes).  variants[0] / variants[1] are the
- * rows-per-block variants of the first (material + x FFT) and last (inverse x
- * FFT + CG update) pass: 0 default, 1 half, 2 double, -1 = choose by timing
- * the candidates on the handle's buffers at the next solve (the default; the
- * choice is cached per grid and precision).  rve_schedule also returns the
- * measured candidate times candidate_ms[2][3] (may be NULL). */
+/* Schedule of the FFT passes: tile shapes, threads and radix schedules.
+ * variants[RVE_SCHED_PASSES] holds
+ *  [0] the first pass (material + x FFT): 0 default rows per block, 1 half,
+ *      2 double; with n_x >= 64 also 3 default rows and 4 half rows with one
+ *      thread per 16-byte load unit of the tile;
+ *  [1] the last pass (inverse x FFT + CG update): 0 default rows, 1 half, 2 double;
+ *  [2] the split N = N1 * N2 of the four-step FFT along the last axis (y in
+ *      2D, z in 3D; the pass that applies the projection): 0 the most square
+ *      split, 1 half N1 and twice N2 (16 = 2 x 8, 32 = 2 x 16, 64 = 4 x 16,
+ *      128 = 4 x 32, 256 = 8 x 32; lengths 512 and 1024 have only split 0);
+ *  [3] in 3D the same choice for the y transforms (0 or 1); 0 in 2D.
+ * -1 = choose by timing the candidates on the handle's buffers at the next
+ * solve (the default; the choice is cached per grid and precision for the
+ * process).  rve_set_schedule rejects a variant the grid does not have.
+ * rve_schedule also returns the measured candidate times
+ * candidate_ms[RVE_SCHED_PASSES][RVE_SCHED_VARIANTS] (0 where a candidate does
+ * not exist or was not timed; may be NULL). */
+enum { RVE_SCHED_PASSES = 4, RVE_SCHED_VARIANTS = 5 };
 int rve_schedule(rve_t h, int* variants, float* candidate_ms);
 int rve_set_schedule(rve_t h, const int* variants);
 
@@ -328,12 +346,18 @@ int rve_batch_effective_tangent(rve_batch_t b, int index, double* C);
  *  cuda_stream  stream to run on (NULL = default stream).
  * Scratch: one static device array of about 1.6 MB (spectrum, tables and a
  * state record), which every GPU that loads the library holds until the process
- * exits.  The first call on a device looks up that array's device address
+ * exits.  That memory is taken when the library's device code is loaded on a
+ * device: with lazy module loading (the CUDA default) this happens at the first
+ * call on that device (or at the first use of any other entry point there), so
+ * a caller that must not allocate later makes one call at set-up time.  The
+ * first call on a device also looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array and it keeps the contents of
- * the last call (each call rewrites everything it reads), so calls that overlap
- * on the GPU -- on different streams, or from different host threads -- race;
- * serialise them.  Returns without waiting for the GPU. */
+ * any stream capture.  Later calls copy nothing from the host: the tables and
+ * the state record are written by a small kernel.  All calls share the array
+ * and it keeps the contents of the last call (each call rewrites everything it
+ * reads), so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race; serialise them.  Not usable after
+ * cudaDeviceReset on that device.  Returns without waiting for the GPU. */
 int rve_apply_operator_2d_static(const int64_t* n, const double* length, const float* E, double nu,
                                  const float* p, float* q, int apply_material, void* cuda_stream);
 

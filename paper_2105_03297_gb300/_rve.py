@@ -241,15 +241,20 @@ class RVE:
         _check(load().rve_get_strain(self.h, int(load_case), p, flag), "rve_get_strain")
         return out
 
-    def schedule(self):
-        """(variants of passes A and E, candidate times [2][3] in ms)."""
-        v = (C.c_int * 2)()
-        t = (C.c_float * 6)()
-        _check(load().rve_schedule(self.h, v, t), "rve_schedule")
-        return [v[0], v[1]], [[t[0], t[1], t[2]], [t[3], t[4], t[5]]]
+    SCHED_PASSES, SCHED_VARIANTS = 4, 5
 
-    def set_schedule(self, var_a, var_e):
-        v = (C.c_int * 2)(int(var_a), int(var_e))
+    def schedule(self):
+        """(variants [pass A, pass E, split of pass C's axis, split of the y axis],
+        candidate times [4][5] in ms)."""
+        v = (C.c_int * self.SCHED_PASSES)()
+        t = (C.c_float * (self.SCHED_PASSES * self.SCHED_VARIANTS))()
+        _check(load().rve_schedule(self.h, v, t), "rve_schedule")
+        W = self.SCHED_VARIANTS
+        return list(v), [list(t[w * W:(w + 1) * W]) for w in range(self.SCHED_PASSES)]
+
+    def set_schedule(self, var_a, var_e, var_c=0, var_y=0):
+        """Force the schedule (-1 = autotune that entry at the next solve)."""
+        v = (C.c_int * self.SCHED_PASSES)(int(var_a), int(var_e), int(var_c), int(var_y))
         _check(load().rve_set_schedule(self.h, v), "rve_set_schedule")
 
     FORMS = {"stress": 0, "factored": 1, "nodal": 2}

@@ -440,8 +440,8 @@ cudaError_t launch_force_stencil(const PassArgs<T>& a, const T* pold, T* pnew, T
     const int tx = a.n[0] < kFX ? a.n[0] : kFX, ty = a.n[1] < kFY ? a.n[1] : kFY;
     const int tz = a.n[2] < kFZ ? a.n[2] : kFZ;
     const size_t sm = force_smem_3d<T>();
-    static bool attr = false;
-    if (!attr) { set_smem_attrs(force_stencil_3d<T>, sm); attr = true; }
+    static DeviceOnce attr;
+    attr.run(current_device(), [&] { set_smem_attrs(force_stencil_3d<T>, sm); });
     dim3 grid(a.n[0] / tx, a.n[1] / ty, (a.n[2] / tz) * a.L);
     force_stencil_3d<T><<<grid, kFNT, sm, s>>>(a, a.r, pold, pnew, a.x, f);
   } else {

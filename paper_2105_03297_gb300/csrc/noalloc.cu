@@ -11,6 +11,12 @@
 // array of fixed size.  It calls no cudaMalloc, cudaFree or other allocating
 // routine.  The kernels are the same three 2D pass kernels that
 // rve_apply_operator uses, so the results are the same.
+//
+// Device memory is still taken once per device, at the first use of the
+// library's device code there: with lazy module loading (the CUDA default)
+// the module that holds the scratch array is loaded into the device's context
+// by the first call, so the first call should be made at set-up time.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -32,9 +38,32 @@ constexpr size_t kStaticScratchBytes = kSpecBytes + kTableBytes + 256;
 // Held by every device that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_rve_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
 // Device address of g_rve_scratch, per device (nullptr = not set up yet).
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
+DeviceOnce g_scratch_once;
+
+// Phase tables exp(+2 pi i j / n) of both axes, twiddle tables exp(-2 pi i j / n),
+// and a fresh CG-state record (active, everything else zero), written on the
+// device so that a call copies nothing from the host.  sincospi is CUDA's own
+// FP64 function; its results are rounded to FP32 like the host tables of the
+// handle path.
+__global__ void fill_static_tables(float2* tables, CgState* cg, int nx, int ny) {
+  const int len[2] = {nx, ny};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * kStaticMaxN; i += gridDim.x * blockDim.x) {
+    const int a = i / kStaticMaxN, j = i % kStaticMaxN;
+    if (j < len[a]) {
+      double sn, cs;
+      sincospi(2.0 * (double)j / (double)len[a], &sn, &cs);
+      tables[a * kStaticMaxN + j] = make_float2((float)cs, (float)sn);             // exp(+i ang)
+      tables[(2 + a) * kStaticMaxN + j] = make_float2((float)cs, (float)-sn);      // exp(-i ang)
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    CgState st{};
+    st.active = 1;
+    *cg = st;
+  }
+}
 
 bool pow2_in(int64_t v, int64_t lo, int64_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
@@ -52,36 +81,27 @@ extern "C" int rve_apply_operator_2d_static(const int64_t* n, const double* leng
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { cudaGetLastError(); return RVE_ERR_CUDA; }
   // Set-up, once per device, with that device current: the device address of
-  // the static array (its name is only a host-side stand-in).
-  if (!g_scratch_ptr[dev]) {
+  // the static array (its name is only a host-side stand-in).  The kernel
+  // attributes of the pass kernels are likewise set once per device by their
+  // launchers.
+  g_scratch_once.run(dev, [&] {
     void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_rve_scratch) != cudaSuccess || !ptr) { cudaGetLastError(); return RVE_ERR_CUDA; }
-    g_scratch_ptr[dev] = ptr;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    if (cudaGetSymbolAddress(&ptr, g_rve_scratch) != cudaSuccess || !ptr) { cudaGetLastError(); ptr = nullptr; }
+    g_scratch_ptr[dev].store(ptr);
+  });
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev].load());
+  if (!base) return RVE_ERR_CUDA;
   float2* spec = reinterpret_cast<float2*>(base);
   float2* tables = reinterpret_cast<float2*>(base + kSpecBytes);   // ph_x, ph_y, tw_x, tw_y
   CgState* cg = reinterpret_cast<CgState*>(base + kSpecBytes + kTableBytes);
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
   const int nx = (int)n[0], ny = (int)n[1];
-  // Host tables on the stack (FP64 libm, rounded to FP32), copied into the scratch.
-  float2 host_tab[4 * kStaticMaxN];
-  const int len[2] = {nx, ny};
-  for (int a = 0; a < 2; ++a)
-    for (int j = 0; j < len[a]; ++j) {
-      const double ang = 2.0 * M_PI * (double)j / (double)len[a];
-      host_tab[a * kStaticMaxN + j] = make_float2((float)std::cos(ang), (float)std::sin(ang));         // exp(+i ang)
-      host_tab[(2 + a) * kStaticMaxN + j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));  // exp(-i ang)
-    }
-  CgState st;
-  std::memset(&st, 0, sizeof(st));
-  st.active = 1;
-  // Both copies come from pageable host memory, so they have completed reading
-  // the stack buffers when cudaMemcpyAsync returns.
-  cudaError_t e = cudaMemcpyAsync(tables, host_tab, sizeof(host_tab), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cg, &st, sizeof(st), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) { cudaGetLastError(); return RVE_ERR_CUDA; }
+  // Tables and CG state of this call, written on the device (the scratch keeps
+  // the previous call's contents).
+  fill_static_tables<<<4, 128, 0, s>>>(tables, cg, nx, ny);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return RVE_ERR_CUDA;
 
   PassArgs<float> a;
   std::memset(&a, 0, sizeof(a));

@@ -593,8 +593,8 @@ cudaError_t launch_nodal_force(const PassArgs<T>& a, const T* rho, const T* pold
     const int tx = a.n[0] < kNX ? a.n[0] : kNX, ty = a.n[1] < kNY ? a.n[1] : kNY;
     const int tz = a.n[2] < kNZ ? a.n[2] : kNZ;
     const size_t sm = nodal_force_smem_3d_v2<T>();
-    static bool attr = false;
-    if (!attr) { set_smem_attrs(nodal_force_3d<T>, sm); attr = true; }
+    static DeviceOnce attr;
+    attr.run(current_device(), [&] { set_smem_attrs(nodal_force_3d<T>, sm); });
     dim3 grid(a.n[0] / tx, a.n[1] / ty, (a.n[2] / tz) * a.L);
     nodal_force_3d<T><<<grid, kNNT, sm, s>>>(a, rho, pold, pnew, xi, f);
   } else {

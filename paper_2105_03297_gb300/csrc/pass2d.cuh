@@ -204,8 +204,15 @@ __device__ __forceinline__ void pass_a_store(const cplx<T>* buf, int gs, cplx<T>
 // ---------------------------------------------------------------- pass A
 // grid (n_y/TY, groups, L), groups = n_q element blocks (n_s components each)
 // or one block of D nodal components (A_NODAL).
+// Resident blocks per SM the register budget of pass A is sized for.
+template <typename T, int NT> __host__ __device__ constexpr int pass_a2_min_blocks() {
+  return sizeof(T) != 4 ? 1 : NT <= 512 ? 2 : 1;
+}
+
+// NT is either the FFT's thread count or (tile variants 3, 4) the number of
+// load units of the tile, so that every thread streams exactly one unit.
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pass_a_2d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, pass_a2_min_blocks<T, NT>()) pass_a_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 3;
@@ -301,12 +308,12 @@ __device__ __forceinline__ void project_2d(cplx<T>* s, cplx<T> ex, cplx<T> ey, T
 // FFT reads the column straight from the spectrum, the inverse FFT writes it
 // straight back; only the middle transposes and the projection use shared
 // memory.
-template <typename T, int NY, int NQ, int NT>
+template <typename T, int NY, int NQ, int NT, int V = 0>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_c_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 3 * NQ;   // 6 for the finite elements and two-point Fourier, 3 for one point,
                               // 9 for finite-strain gradients (8 + padding)
-  constexpr int LD = FftSplit<NY>::LD;
+  constexpr int LD = FftSplit<NY, V>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [M][LD]
   const int kx = blockIdx.x, l = blockIdx.y;
@@ -320,8 +327,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_c_2d(PassArgs
   const int64_t cstride = (int64_t)KX * NY;
   auto ld_g = [&](int c, int y) -> C { return col[c * cstride + y]; };
   auto st_s = [&](int c, int k, C v) { buf[c * LD + k] = v; };
-  if (cin == M) fft4<T, NY, M, LD, NT, -1, false, true, false, false>(buf, a.tw[1], ld_g, st_s);
-  else fft4<T, NY, 2, LD, NT, -1, false, true, false, false>(buf, a.tw[1], ld_g, st_s);
+  if (cin == M) fft4<T, NY, M, LD, NT, -1, false, true, false, false, V>(buf, a.tw[1], ld_g, st_s);
+  else fft4<T, NY, 2, LD, NT, -1, false, true, false, false, V>(buf, a.tw[1], ld_g, st_s);
 
   const C ex = a.ph[0][kx];
   for (int ky = threadIdx.x; ky < NY; ky += NT) {
@@ -354,8 +361,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_c_2d(PassArgs
   __syncthreads();
   auto ld_s = [&](int c, int y) -> C { return buf[c * LD + y]; };
   auto st_g = [&](int c, int k, C v) { col[c * cstride + k] = v; };
-  if (cout == M) fft4<T, NY, M, LD, NT, +1, true, false, false, false>(buf, a.tw[1], ld_s, st_g);
-  else fft4<T, NY, 2, LD, NT, +1, true, false, false, false>(buf, a.tw[1], ld_s, st_g);
+  if (cout == M) fft4<T, NY, M, LD, NT, +1, true, false, false, false, V>(buf, a.tw[1], ld_s, st_g);
+  else fft4<T, NY, 2, LD, NT, +1, true, false, false, false, V>(buf, a.tw[1], ld_s, st_g);
 }
 
 // Pass C for the nodal solve w^ = (B^H B)^-1 f^ (P_SOLVE, 2 components in and
@@ -407,21 +414,38 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) pass_c_2d_nodal(Pa
 // Pass E body shared by 2D and 3D: load the (k, y-pair) spectra of ge
 // components into packed rows (component j at src + j*comp_stride +
 // k*k_stride + y-offset, rows j*NP + pr), ready for the inverse FFT.
+// Each thread has up to UB of its loads in flight before it writes any of
+// them to shared memory (a load per loop trip would leave one in flight).
 template <typename T, int NX, int TY, int NT, int LD>
 __device__ __forceinline__ void pass_e_unpack(cplx<T>* buf, const cplx<T>* src, int ge, int64_t comp_stride,
                                               int64_t k_stride) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
-  for (int i = threadIdx.x; i < ge * KX * NP; i += NT) {
-    const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
-    C ab[2];
-    cload2<T>(ab, src + j * comp_stride + (int64_t)k * k_stride + 2 * pr);
-    C xa = ab[0], xb = ab[1];
-    if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }  // C2R ignores these imaginary parts
-    C* row = buf + (j * NP + pr) * LD;
-    row[k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);                                  // X_a + i X_b
-    if (k > 0 && k < NX / 2) row[NX - k] = mkc<T>(xa.x + xb.y, xb.x - xa.y);    // conj(X_a) + i conj(X_b)
+  constexpr int UB = 8;
+  const int total = ge * KX * NP;
+  for (int i0 = threadIdx.x; i0 < total; i0 += UB * NT) {
+    C ab[UB][2];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int i = i0 + u * NT;
+      if (i < total) {
+        const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
+        cload2<T>(ab[u], src + j * comp_stride + (int64_t)k * k_stride + 2 * pr);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int i = i0 + u * NT;
+      if (i < total) {
+        const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
+        C xa = ab[u][0], xb = ab[u][1];
+        if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }  // C2R ignores these imaginary parts
+        C* row = buf + (j * NP + pr) * LD;
+        row[k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);                                  // X_a + i X_b
+        if (k > 0 && k < NX / 2) row[NX - k] = mkc<T>(xa.x + xb.y, xb.x - xa.y);    // conj(X_a) + i conj(X_b)
+      }
+    }
   }
 }
 
@@ -532,7 +556,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pas
   const T alpha = (a.emode == E_CG) ? (T)cg->alpha : (T)0;
   auto ld_s = [&](int b, int x) -> C { return buf[b * LD + x]; };
   PassEStore<T, NX, NP> st{&a, ge, (int64_t)y0 * NX, ((int64_t)l * a.m + c0) * N, (int64_t)l * 2 * N, alpha, &acc};
-  fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
+  fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, 0, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
                                                                                                   ld_s, st);
 
   if (a.emode == E_CG || a.emode == E_INIT) {
@@ -589,13 +613,15 @@ template <typename T> constexpr int tile_rows(int v) {
   return v == 1 ? Tile2D<T>::TY / 2 : v == 2 ? Tile2D<T>::TY * 2 : Tile2D<T>::TY;
 }
 
-template <typename T, int NX, int TY>
+template <typename T, int NX, int TY, bool BY_UNITS = false>
 cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
+  constexpr int NF = fft_threads<NX, 3 * (TY / 2)>();
+  constexpr int NU = ((TY / 2) * (NX / Vec16<T>::n) + 31) / 32 * 32;   // load units of a tile
+  constexpr int NT = (BY_UNITS && NU > NF && NU <= 1024) ? NU : NF;
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_2d<T, NX, TY, NT>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
   dim3 grid(a.n[1] / TY, a.amode == A_NODAL ? 1 : a.nq, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -605,8 +631,8 @@ cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_2d<T, NX, TY, NT>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
   dim3 grid(a.n[1] / TY, (a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : a.nq, a.L);
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -616,6 +642,8 @@ cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   if constexpr (NX >= 64) {
     if (a.var_a == 1) return launch_a_2d_t<T, NX, tile_rows<T>(1)>(a, s);
     if (a.var_a == 2 && a.n[1] >= tile_rows<T>(2)) return launch_a_2d_t<T, NX, tile_rows<T>(2)>(a, s);
+    if (a.var_a == 3) return launch_a_2d_t<T, NX, tile_rows<T>(0), true>(a, s);
+    if (a.var_a == 4) return launch_a_2d_t<T, NX, tile_rows<T>(1), true>(a, s);
   }
   return launch_a_2d_t<T, NX, tile_rows<T>(0)>(a, s);
 }
@@ -627,6 +655,19 @@ cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   }
   return launch_e_2d_t<T, NX, tile_rows<T>(0)>(a, s);
 }
+// Pass C of the finite elements (two triangles) with split variant V (a.var_c).
+template <typename T, int NY, int V>
+cudaError_t launch_c_2d_v(const PassArgs<T>& a, cudaStream_t s) {
+  constexpr int NT = fft_threads<NY, 6, V>();
+  const size_t sm = sizeof(cplx<T>) * 6 * FftSplit<NY, V>::LD;
+  auto k = pass_c_2d<T, NY, 2, NT, V>;
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
+  dim3 grid(a.kx, a.L);
+  k<<<grid, NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int NY>
 cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   if (a.pmode == P_SOLVE) {
@@ -634,8 +675,8 @@ cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int NTn = fft_threads<NY, 2 * P>();
     const size_t smn = sizeof(cplx<T>) * 2 * P * FftSplit<NY>::LD;
     auto kn = pass_c_2d_nodal<T, NY, P, NTn>;
-    static bool attr_n = false;
-    if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
+    static DeviceOnce attr_n;
+    attr_n.run(current_device(), [&] { set_smem_attrs(kn, smn); });
     dim3 gridn((a.kx + P - 1) / P, a.L);
     kn<<<gridn, NTn, smn, s>>>(a);
     return cudaGetLastError();
@@ -644,8 +685,8 @@ cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int NT3 = fft_threads<NY, 9>();
     const size_t sm3 = sizeof(cplx<T>) * 9 * FftSplit<NY>::LD;
     auto k3 = pass_c_2d<T, NY, 3, NT3>;
-    static bool attr3 = false;
-    if (!attr3) { set_smem_attrs(k3, sm3); attr3 = true; }
+    static DeviceOnce attr3;
+    attr3.run(current_device(), [&] { set_smem_attrs(k3, sm3); });
     k3<<<dim3(a.kx, a.L), NT3, sm3, s>>>(a);
     return cudaGetLastError();
   }
@@ -653,19 +694,15 @@ cudaError_t launch_c_2d_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int NT1 = fft_threads<NY, 3>();
     const size_t sm1 = sizeof(cplx<T>) * 3 * FftSplit<NY>::LD;
     auto k1 = pass_c_2d<T, NY, 1, NT1>;
-    static bool attr1 = false;
-    if (!attr1) { set_smem_attrs(k1, sm1); attr1 = true; }
+    static DeviceOnce attr1;
+    attr1.run(current_device(), [&] { set_smem_attrs(k1, sm1); });
     k1<<<dim3(a.kx, a.L), NT1, sm1, s>>>(a);
     return cudaGetLastError();
   }
-  constexpr int NT = fft_threads<NY, 6>();
-  const size_t sm = sizeof(cplx<T>) * 6 * FftSplit<NY>::LD;
-  auto k = pass_c_2d<T, NY, 2, NT>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.kx, a.L);
-  k<<<grid, NT, sm, s>>>(a);
-  return cudaGetLastError();
+  if constexpr (fft_split_count<NY>() > 1) {
+    if (a.var_c == 1) return launch_c_2d_v<T, NY, 1>(a, s);
+  }
+  return launch_c_2d_v<T, NY, 0>(a, s);
 }
 
 #define RVE_DISPATCH_N(nval, FN, ...)                      \

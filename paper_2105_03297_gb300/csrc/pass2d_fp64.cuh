@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(kRNT) residual_2d(Fp64Args a) {
 inline cudaError_t launch_residual_2d(const Fp64Args& a, cudaStream_t s) {
   const int tx = a.n[0] < kRX ? a.n[0] : kRX, ty = a.n[1] < kRY ? a.n[1] : kRY;
   const size_t sm = residual_2d_smem();
-  static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(residual_2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { cudaFuncSetAttribute(residual_2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); });
   dim3 grid(a.n[0] / tx, (a.n[1] / ty) * a.L);
   residual_2d<<<grid, kRNT, sm, s>>>(a);
   return cudaGetLastError();

@@ -27,9 +27,16 @@ __host__ __device__ constexpr int kuhn_perm(int t, int i) {
 }
 
 // ---------------------------------------------------------------- pass A
+// Resident blocks per SM the register budget is sized for.
+template <typename T, int NT> __host__ __device__ constexpr int pass_a_min_blocks() {
+  return sizeof(T) != 4 ? 1 : NT <= 384 ? 3 : NT <= 512 ? 2 : 1;
+}
+
 // grid (n_y/TY, n_z, L*G), G = 6 tetrahedra (6 components each) or 1 (nodal, 3).
+// NT is either the FFT's thread count or (tile variants 3, 4) the number of
+// load units of the tile, so that every thread streams exactly one unit.
 template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pass_a_3d(PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, pass_a_min_blocks<T, NT>()) pass_a_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 6;
@@ -75,11 +82,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
 // ---------------------------------------------------------------- pass B / D
 // FFT along y.  grid (n_z/TZB, n_x/2+1, L*Cc).  FWD: spec1 pencils -> spec2
 // chunks; !FWD: spec2 chunks -> spec1 pencils.
-template <typename T, int NY, int TZB, int NT, bool FWD>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_y_3d(PassArgs<T> a, int Cc) {
+template <typename T, int NY, int TZB, int NT, bool FWD, int V = 0>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT <= 256 ? 4 : 2) : 1) pass_y_3d(PassArgs<T> a, int Cc) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LD = FftSplit<NY>::LDO;  // odd: the chunk transposes are conflict-free
+  constexpr int LD = FftSplit<NY, V>::LDO;  // odd: the chunk transposes are conflict-free
   C* buf = reinterpret_cast<C*>(smem_raw);  // [TZB][LD]
   const int l = blockIdx.z / Cc, c = blockIdx.z % Cc;
   const int kx = blockIdx.y, z0 = blockIdx.x * TZB;
@@ -94,11 +101,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) pass_y_3d(PassArgs
     // step 1 reads whole y-pencils, step 2 writes z-chunks (zz fastest)
     auto ld = [&](int zz, int y) -> C { return pencils[(int64_t)zz * NY + y]; };
     auto st = [&](int zz, int k, C v) { chunks[(int64_t)k * nz + zz] = v; };
-    fft4<T, NY, TZB, LD, NT, -1, false, false, false, true>(buf, a.tw[1], ld, st);
+    fft4<T, NY, TZB, LD, NT, -1, false, false, false, true, V>(buf, a.tw[1], ld, st);
   } else {
     auto ld = [&](int zz, int k) -> C { return chunks[(int64_t)k * nz + zz]; };
     auto st = [&](int zz, int y, C v) { pencils[(int64_t)zz * NY + y] = v; };
-    fft4<T, NY, TZB, LD, NT, +1, false, false, true, false>(buf, a.tw[1], ld, st);
+    fft4<T, NY, TZB, LD, NT, +1, false, false, true, false, V>(buf, a.tw[1], ld, st);
   }
 }
 
@@ -300,12 +307,24 @@ __device__ __forceinline__ void project_3d_pair(cplx<T>* col, const cplx<T>* e, 
   }
 }
 
+// Row stride of the pass C buffer: at least the FFT's leading dimension, and
+// chosen so that the two lanes of a wavevector (rows c and c + 18, same
+// column) fall into different halves of a shared-memory bank window: the row
+// offset 18 LD sizeof(complex) is then an odd multiple of 64 bytes and the
+// lane-pair projection's accesses are free of bank conflicts.
+template <typename T, int NZ, int V = 0> __host__ __device__ constexpr int pass_c_ld() {
+  constexpr int base = FftSplit<NZ, V>::LD;
+  constexpr int mod = sizeof(T) == 4 ? 8 : 4, want = sizeof(T) == 4 ? 4 : 2;
+  return base + ((want - base % mod) + mod) % mod;
+}
+
 // grid (n_x/2+1, n_y, L): one (k_x, k_y) pencil of all components per block.
-template <typename T, int NZ, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs<T> a) {
+template <typename T, int NZ, int NT, int V = 0>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 576) ? 2 : 1) pass_c_3d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int M = 36;
-  constexpr int LD = FftSplit<NZ>::LD;
+  constexpr int LD = pass_c_ld<T, NZ, V>();
+  static_assert((18 * LD * (int)sizeof(cplx<T>)) % 128 == 64, "lane pairs must not share a bank");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [M][LD]
   const int kx = blockIdx.x, ky = blockIdx.y, l = blockIdx.z;
@@ -319,8 +338,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
   C* pen = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
   auto ld_g = [&](int c, int z) -> C { return pen[c * stride_c + z]; };
   auto st_s = [&](int c, int k, C v) { buf[c * LD + k] = v; };
-  if (cin == M) fft4<T, NZ, M, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
-  else fft4<T, NZ, 3, LD, NT, -1, false, true, false, false>(buf, a.tw[2], ld_g, st_s);
+  if (cin == M) fft4<T, NZ, M, LD, NT, -1, false, true, false, false, V>(buf, a.tw[2], ld_g, st_s);
+  else fft4<T, NZ, 3, LD, NT, -1, false, true, false, false, V>(buf, a.tw[2], ld_g, st_s);
   C e[3];
   e[0] = a.ph[0][kx];
   e[1] = a.ph[1][ky];
@@ -334,8 +353,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) pass_c_3d(PassArgs
   __syncthreads();
   auto ld_s = [&](int c, int z) -> C { return buf[c * LD + z]; };
   auto st_g = [&](int c, int k, C v) { pen[c * stride_c + k] = v; };
-  if (cout == M) fft4<T, NZ, M, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
-  else fft4<T, NZ, 3, LD, NT, +1, true, false, false, false>(buf, a.tw[2], ld_s, st_g);
+  if (cout == M) fft4<T, NZ, M, LD, NT, +1, true, false, false, false, V>(buf, a.tw[2], ld_s, st_g);
+  else fft4<T, NZ, 3, LD, NT, +1, true, false, false, false, V>(buf, a.tw[2], ld_s, st_g);
 }
 
 // Pass C for the nodal solve w^ = (B^H B)^-1 f^ (P_SOLVE, 3 components in
@@ -499,7 +518,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
   auto ld_s = [&](int b, int x) -> C { return buf[b * LD + x]; };
   PassEStore<T, NX, NP> st{&a, ge, ((int64_t)z * ny + y0) * NX, ((int64_t)l * a.m + c0) * N, (int64_t)l * 3 * N,
                            alpha, &acc};
-  fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
+  fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, 0, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
                                                                                                   ld_s, st);
 
   if (a.emode == E_CG || a.emode == E_INIT) {
@@ -523,13 +542,20 @@ template <typename T> constexpr int tile_rows3(int v) {
   return v == 1 ? Tile3D<T>::TY / 2 : v == 2 ? Tile3D<T>::TY * 2 : Tile3D<T>::TY;
 }
 
-template <typename T, int NX, int TY>
+// Load units of a pass A tile (see pass_a_load: two rows x one 16-byte vector
+// of every component of one half of an element).
+template <typename T, int NX, int TY> constexpr int pass_a_units3() { return 2 * (TY / 2) * (NX / Vec16<T>::n); }
+template <int A, int B> constexpr int max_i() { return A > B ? A : B; }
+
+template <typename T, int NX, int TY, bool BY_UNITS = false>
 cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
+  constexpr int NF = fft_threads<NX, 6 * (TY / 2)>();
+  constexpr int NU = (pass_a_units3<T, NX, TY>() + 31) / 32 * 32;
+  constexpr int NT = BY_UNITS ? (max_i<NF, NU>() > 1024 ? NF : max_i<NF, NU>()) : NF;
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_a_3d<T, NX, TY, NT>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
   dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.amode == A_NODAL ? 1 : a.nq));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
@@ -539,17 +565,21 @@ cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
   auto k = pass_e_3d<T, NX, TY, NT>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
   dim3 grid(a.n[1] / TY, a.n[2], a.L * ((a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : a.nq));
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
+// Tile variants of pass A: 0 default rows per block, 1 half, 2 double (threads
+// = the FFT's); 3 default rows and 4 half rows with one thread per load unit.
 template <typename T, int NX>
 cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   if constexpr (NX >= 64) {
     if (a.var_a == 1) return launch_a_3d_t<T, NX, tile_rows3<T>(1)>(a, s);
     if (a.var_a == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_a_3d_t<T, NX, tile_rows3<T>(2)>(a, s);
+    if (a.var_a == 3) return launch_a_3d_t<T, NX, tile_rows3<T>(0), true>(a, s);
+    if (a.var_a == 4) return launch_a_3d_t<T, NX, tile_rows3<T>(1), true>(a, s);
   }
   return launch_a_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
 }
@@ -561,14 +591,14 @@ cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   }
   return launch_e_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
 }
-template <typename T, int NY, bool FWD>
-cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+template <typename T, int NY, bool FWD, int V>
+cudaError_t launch_y_3d_v(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int TZB = Tile3D<T>::TZB;
-  constexpr int NT = fft_threads<NY, TZB>();
-  const size_t sm = sizeof(cplx<T>) * TZB * FftSplit<NY>::LDO;
-  auto k = pass_y_3d<T, NY, TZB, NT, FWD>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
+  constexpr int NT = fft_threads<NY, TZB, V>();
+  const size_t sm = sizeof(cplx<T>) * TZB * FftSplit<NY, V>::LDO;
+  auto k = pass_y_3d<T, NY, TZB, NT, FWD, V>;
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
   const bool din = (a.pmode == P_NODAL_IN || a.pmode == P_SOLVE);
   const bool dout = (a.pmode == P_NODAL_OUT || a.pmode == P_SOLVE);
   const int Cc = FWD ? (din ? 3 : a.m) : (dout ? 3 : a.m);
@@ -576,12 +606,33 @@ cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   k<<<grid, NT, sm, s>>>(a, Cc);
   return cudaGetLastError();
 }
+// Split variant of the y transforms (passes B and D): a.var_y.
+template <typename T, int NY, bool FWD>
+cudaError_t launch_y_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (fft_split_count<NY>() > 1) {
+    if (a.var_y == 1) return launch_y_3d_v<T, NY, FWD, 1>(a, s);
+  }
+  return launch_y_3d_v<T, NY, FWD, 0>(a, s);
+}
 template <typename T, int NY> cudaError_t launch_yf_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   return launch_y_3d_n<T, NY, true>(a, s);
 }
 template <typename T, int NY> cudaError_t launch_yb_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   return launch_y_3d_n<T, NY, false>(a, s);
 }
+// Pass C of the finite-element stress form with split variant V (a.var_c).
+template <typename T, int NZ, int V>
+cudaError_t launch_c_3d_v(const PassArgs<T>& a, cudaStream_t s) {
+  constexpr int NT = fft_threads<NZ, 36, V>();
+  const size_t sm = sizeof(cplx<T>) * 36 * pass_c_ld<T, NZ, V>();
+  auto k = pass_c_3d<T, NZ, NT, V>;
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
+  dim3 grid(a.kx, a.n[1], a.L);
+  k<<<grid, NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int NZ>
 cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   if (a.pmode == P_SOLVE) {
@@ -589,8 +640,8 @@ cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int NTn = fft_threads<NZ, 3 * P>();
     const size_t smn = sizeof(cplx<T>) * 3 * P * FftSplit<NZ>::LD;
     auto kn = pass_c_3d_nodal<T, NZ, P, NTn>;
-    static bool attr_n = false;
-    if (!attr_n) { set_smem_attrs(kn, smn); attr_n = true; }
+    static DeviceOnce attr_n;
+    attr_n.run(current_device(), [&] { set_smem_attrs(kn, smn); });
     dim3 gridn(a.kx, a.n[1] / P, a.L);
     kn<<<gridn, NTn, smn, s>>>(a);
     return cudaGetLastError();
@@ -600,8 +651,8 @@ cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
     const size_t smf = sizeof(cplx<T>) * 54 * FftSplit<NZ>::LD;
     if (smf > 227 * 1024) return cudaErrorInvalidConfiguration;   // FP64 at n_z = 256
     auto kf = pass_c_3d_fs<T, NZ, NTf>;
-    static bool attrf = false;
-    if (!attrf) { set_smem_attrs(kf, smf); attrf = true; }
+    static DeviceOnce attrf;
+    attrf.run(current_device(), [&] { set_smem_attrs(kf, smf); });
     kf<<<dim3(a.kx, a.n[1], a.L), NTf, smf, s>>>(a);
     return cudaGetLastError();
   }
@@ -609,19 +660,15 @@ cudaError_t launch_c_3d_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int NT1 = fft_threads<NZ, 36>();
     const size_t sm1 = sizeof(cplx<T>) * 36 * FftSplit<NZ>::LD;
     auto k1 = pass_c_3d_q1<T, NZ, NT1>;
-    static bool attr1 = false;
-    if (!attr1) { set_smem_attrs(k1, sm1); attr1 = true; }
+    static DeviceOnce attr1;
+    attr1.run(current_device(), [&] { set_smem_attrs(k1, sm1); });
     k1<<<dim3(a.kx, (a.n[1] + 5) / 6, a.L), NT1, sm1, s>>>(a);
     return cudaGetLastError();
   }
-  constexpr int NT = fft_threads<NZ, 36>();
-  const size_t sm = sizeof(cplx<T>) * 36 * FftSplit<NZ>::LD;
-  auto k = pass_c_3d<T, NZ, NT>;
-  static bool attr = false;
-  if (!attr) { set_smem_attrs(k, sm); attr = true; }
-  dim3 grid(a.kx, a.n[1], a.L);
-  k<<<grid, NT, sm, s>>>(a);
-  return cudaGetLastError();
+  if constexpr (fft_split_count<NZ>() > 1) {
+    if (a.var_c == 1) return launch_c_3d_v<T, NZ, 1>(a, s);
+  }
+  return launch_c_3d_v<T, NZ, 0>(a, s);
 }
 
 #define RVE_DISPATCH_N3(nval, FN, ...)                     \

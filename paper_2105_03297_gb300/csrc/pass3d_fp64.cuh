@@ -223,8 +223,8 @@ inline cudaError_t launch_residual_3d(const Fp64Args& a, cudaStream_t s) {
   const int tx = a.n[0] < kR3X ? a.n[0] : kR3X, ty = a.n[1] < kR3Y ? a.n[1] : kR3Y;
   const int tz = a.n[2] < kR3Z ? a.n[2] : kR3Z;
   const size_t sm = residual_3d_smem();
-  static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(residual_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); attr = true; }
+  static DeviceOnce attr;
+  attr.run(current_device(), [&] { cudaFuncSetAttribute(residual_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); });
   dim3 grid(a.n[0] / tx, a.n[1] / ty, (a.n[2] / tz) * a.L);
   residual_3d<<<grid, kR3NT, sm, s>>>(a);
   return cudaGetLastError();

@@ -15,13 +15,13 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <tuple>
 #include <type_traits>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "../../include/rve.h"
@@ -78,8 +78,11 @@ struct rve_s {
   int64_t t_cnt[RVE_NKINDS] = {0};
   std::vector<Rec>* capturing = nullptr;  // event pairs recorded while capturing a graph
   CgState* cg_h2 = nullptr;               // second pinned copy of the CG state (run-ahead)
-  int var[2] = {-1, -1};                  // tile variants of passes A and E (-1 = autotune at first solve)
-  float tune_ms[2][3] = {{0}};            // measured times of the candidates (last tuning)
+  // schedule: variants of pass A (tile rows / threads), pass E (tile rows), the
+  // FFT split of pass C's axis and of passes B / D (3D); -1 = autotune at the
+  // first solve
+  int var[RVE_SCHED_PASSES] = {-1, -1, -1, -1};
+  float tune_ms[RVE_SCHED_PASSES][RVE_SCHED_VARIANTS] = {{0}};  // candidate times of the last tuning
   int op_form = RVE_FORM_STRESS;          // order of the operator inside projected CG
   int deriv = D_FE;                       // discrete derivative of the projection (RVE_DERIV_*)
   int finite = 0;                         // RVE_FINITE_STRAIN: fields are deformation gradients
@@ -156,6 +159,27 @@ void flush_timing(rve_s* h) {
 }
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Makes `device` current for the lifetime of the object (an API call, a batch
+// group's host thread) and restores the thread's previous device afterwards;
+// a negative index leaves the current device alone.
+struct DeviceScope {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceScope(int device) {
+    if (device < 0) return;
+    if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+    if (prev != device) {
+      changed = (cudaSetDevice(device) == cudaSuccess);
+      if (!changed) cudaGetLastError();
+    }
+  }
+  ~DeviceScope() {
+    if (changed && prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+};
 
 void free_dev(void*& p) { if (p) { cudaFree(p); p = nullptr; } }
 template <typename P> void free_devp(P*& p) { if (p) { cudaFree(p); p = nullptr; } }
@@ -302,6 +326,8 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   a.cg = h->cg; a.part = h->part; a.part_stride = h->part_stride;
   a.var_a = h->var[0] < 0 ? 0 : h->var[0];
   a.var_e = h->var[1] < 0 ? 0 : h->var[1];
+  a.var_c = h->var[2] < 0 ? 0 : h->var[2];
+  a.var_y = h->var[3] < 0 ? 0 : h->var[3];
   return a;
 }
 
@@ -436,19 +462,46 @@ int write_state(rve_s* h, int L) {
   return RVE_OK;
 }
 
-// ---- autotuner: tile variants of passes A and E ------------------------
-// Candidates: rows per block = default, half, double.  Each is timed on the
-// handle's own buffers (operator-application modes on a zeroed field, 2 warm-up
-// and 3 timed launches, CUDA events on the handle's stream) and the fastest is
-// kept; choices are cached per (dimension, grid, precision) for the process.
+// ---- autotuner: the schedule of the FFT passes --------------------------
+// Candidates per pass (rve_sched_candidates): pass A rows per block (default,
+// half, double) and one thread per load unit at the default and half rows;
+// pass E rows per block (default, half, double); the FFT split (radix
+// schedule) of pass C's axis; in 3D the split of the y axis (passes B and D,
+// timed together).  Each candidate is timed on the handle's own buffers
+// (operator-application modes on a zeroed field, 2 warm-up and 3 timed
+// launches, CUDA events on the handle's stream), passes in the order A, E, C,
+// B/D with the winners of the earlier ones, and the fastest is kept; choices
+// are cached per (dimension, grid, precision) for the process.
 struct TuneKey {
   int dim, n0, n1, n2, tsize;
   bool operator<(const TuneKey& o) const {
     return std::tie(dim, n0, n1, n2, tsize) < std::tie(o.dim, o.n0, o.n1, o.n2, o.tsize);
   }
 };
-std::map<TuneKey, std::pair<int, int>> g_tuned;
+std::map<TuneKey, std::array<int, RVE_SCHED_PASSES>> g_tuned;
 std::mutex g_tune_mutex;
+
+int split_count(int n) {
+  switch (n) {
+    case 16: return fft_split_count<16>();
+    case 32: return fft_split_count<32>();
+    case 64: return fft_split_count<64>();
+    case 128: return fft_split_count<128>();
+    case 256: return fft_split_count<256>();
+    case 512: return fft_split_count<512>();
+    default: return fft_split_count<1024>();
+  }
+}
+
+// Number of candidates of schedule entry `which` for a handle.
+int rve_sched_candidates(const rve_s* h, int which) {
+  switch (which) {
+    case 0: return h->n[0] >= 64 ? 5 : 3;
+    case 1: return 3;
+    case 2: return split_count(h->n[h->dim - 1]);
+    default: return h->dim == 3 ? split_count(h->n[1]) : 1;
+  }
+}
 
 template <typename T> int autotune(rve_s* h) {
   const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], (int)h->tsize};
@@ -456,35 +509,57 @@ template <typename T> int autotune(rve_s* h) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      if (h->var[0] < 0) h->var[0] = it->second.first;
-      if (h->var[1] < 0) h->var[1] = it->second.second;
+      for (int w = 0; w < RVE_SCHED_PASSES; ++w)
+        if (h->var[w] < 0) h->var[w] = it->second[w];
       return RVE_OK;
     }
   }
+  // passes A and E are timed in their CG-iteration modes (A: direction update,
+  // deferred x update, material, x FFT, <p, C p>; E: inverse x FFT, r update,
+  // <r, r>) on zeroed vectors of one load case; the CG state they finalise is
+  // reset by the solve that follows
   const size_t fld = (size_t)h->m * h->N * h->tsize;
   CK(cudaMemsetAsync(h->fbuf, 0, fld, h->stream));
+  CK(cudaMemsetAsync(h->r, 0, fld, h->stream));
+  CK(cudaMemsetAsync(h->p, 0, fld, h->stream));
+  CK(cudaMemsetAsync(h->x, 0, fld, h->stream));
   std::memset(h->cg_h, 0, sizeof(CgState));
   h->cg_h[0].active = 1;
+  h->cg_h[0].it = 1;
   int rc = write_state(h, 1);
   if (rc) return rc;
   PassArgs<T> a = pass_args<T>(h, 1, h->u, h->emac_d);
-  a.cgphase = 0; a.amode = A_FIELD; a.pmode = P_G; a.emode = E_OUT;
+  a.cgphase = 0; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
   a.in = (const T*)h->fbuf; a.out = (T*)h->x;
+  a.var_a = a.var_e = a.var_c = a.var_y = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  int best[2] = {0, 0};
-  for (int which = 0; which < 2; ++which) {
+  const bool d3 = (h->dim == 3);
+  auto pass_a_l = [&]() { return d3 ? launch_pass_a_3d<T>(a, h->stream) : launch_pass_a_2d<T>(a, h->stream); };
+  auto pass_b_l = [&]() { return d3 ? launch_pass_b_3d<T>(a, h->stream) : cudaSuccess; };
+  auto pass_c_l = [&]() { return d3 ? launch_pass_c_3d<T>(a, h->stream) : launch_pass_c_2d<T>(a, h->stream); };
+  auto pass_d_l = [&]() { return d3 ? launch_pass_d_3d<T>(a, h->stream) : cudaSuccess; };
+  auto pass_e_l = [&]() { return d3 ? launch_pass_e_3d<T>(a, h->stream) : launch_pass_e_2d<T>(a, h->stream); };
+  int best[RVE_SCHED_PASSES] = {0, 0, 0, 0};
+  for (int w = 0; w < RVE_SCHED_PASSES; ++w)
+    for (int v = 0; v < RVE_SCHED_VARIANTS; ++v) h->tune_ms[w][v] = 0.f;
+  for (int which = 0; which < RVE_SCHED_PASSES; ++which) {
+    const int nc = rve_sched_candidates(h, which);
     float best_ms = 1e30f;
-    for (int v = 0; v < 3; ++v) {
-      a.var_a = which == 0 ? v : best[0];
-      a.var_e = which == 1 ? v : 0;
+    for (int v = 0; v < nc; ++v) {
+      int* slot = which == 0 ? &a.var_a : which == 1 ? &a.var_e : which == 2 ? &a.var_c : &a.var_y;
+      *slot = v;
       auto one = [&]() -> cudaError_t {
-        if (which == 0) return h->dim == 2 ? launch_pass_a_2d<T>(a, h->stream) : launch_pass_a_3d<T>(a, h->stream);
-        return h->dim == 2 ? launch_pass_e_2d<T>(a, h->stream) : launch_pass_e_3d<T>(a, h->stream);
+        if (which == 0) return pass_a_l();
+        if (which == 1) return pass_e_l();
+        if (which == 2) return pass_c_l();
+        cudaError_t e = pass_b_l();
+        return e == cudaSuccess ? pass_d_l() : e;
       };
-      // pass E reads the x-spectrum: let pass A fill it first
-      if (which == 1) CK(h->dim == 2 ? launch_pass_a_2d<T>(a, h->stream) : launch_pass_a_3d<T>(a, h->stream));
+      // the later passes read the spectra the earlier ones write: fill them once
+      if (which >= 1) CK(pass_a_l());
+      if (which >= 2) CK(pass_b_l());
       for (int k = 0; k < 2; ++k) CK(one());
       CK(cudaEventRecord(e0, h->stream));
       for (int k = 0; k < 3; ++k) CK(one());
@@ -495,13 +570,17 @@ template <typename T> int autotune(rve_s* h) {
       h->tune_ms[which][v] = ms / 3.0f;
       if (ms < best_ms) { best_ms = ms; best[which] = v; }
     }
+    *(which == 0 ? &a.var_a : which == 1 ? &a.var_e : which == 2 ? &a.var_c : &a.var_y) = best[which];
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (h->var[0] < 0) h->var[0] = best[0];
-  if (h->var[1] < 0) h->var[1] = best[1];
+  std::array<int, RVE_SCHED_PASSES> chosen;
+  for (int w = 0; w < RVE_SCHED_PASSES; ++w) {
+    if (h->var[w] < 0) h->var[w] = best[w];
+    chosen[w] = best[w];
+  }
   std::lock_guard<std::mutex> lk(g_tune_mutex);
-  g_tuned[key] = {best[0], best[1]};
+  g_tuned[key] = chosen;
   return RVE_OK;
 }
 
@@ -609,31 +688,51 @@ template <typename T> struct CgRunner {
   }
 };
 
-// The solve driver.  u_out [L][D][N] receives the FP64 nodal fluctuation.
-template <typename T>
-int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max_iter, rve_info* info,
-               double* u_out, double* emac_dev) {
-  const bool mixed = (h->tsize == 4);
-  CK(cudaMemcpyAsync(emac_dev, emac_host, (size_t)L * h->ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemsetAsync(u_out, 0, (size_t)L * h->D * h->N * sizeof(double), h->stream));
-  const double inner_tol = mixed ? std::fmax(rel_tol, 2e-5) : rel_tol;
-  const int max_outer = mixed ? 12 : 6;
-  std::vector<double> f0(L, 0.0), frel(L, 0.0), cgrel(L, 0.0);
-  std::vector<int> iters(L, 0), steps(L, 0), bad(L, 0), active(L, 1), floor_hit(L, 0);
-  std::memset(h->cg_h, 0, (size_t)L * sizeof(CgState));
-  for (int l = 0; l < L; ++l) { h->cg_h[l].active = 1; h->cg_h[l].status = ST_RUN; }
-  int rc = write_state(h, L);
-  if (rc) return rc;
+// The solve driver, in phases so that a batch can run several handles in
+// lockstep (FeSolve::begin, then per refinement step outer() -> the inner
+// projected CG -> after_inner(), then finish()).  u_out [L][D][N] receives the
+// FP64 nodal fluctuation.
+template <typename T> struct FeSolve {
+  rve_s* h;
+  int L;
+  double rel_tol;
+  int max_iter;
+  double* u_out;
+  double* emac_dev;
+  bool mixed;
+  double inner_tol;
+  int max_outer;
+  int step = 0;
+  std::vector<double> f0, frel, cgrel;
+  std::vector<int> iters, steps, bad, active, floor_hit;
+  Fp64Args fa;
+  PassArgs<T> a;
 
-  Fp64Args fa = fp64_args(h, L, u_out, emac_dev, h->cg);
-  PassArgs<T> a = pass_args<T>(h, L, u_out, emac_dev);
-  const int check_every = 8;  // even: the factored form alternates its direction buffers
-  std::unique_ptr<CgRunner<T>> runner;  // built at the first inner solve, reused by later ones
+  FeSolve(rve_s* h_, int L_, double rel_tol_, int max_iter_, double* u_out_, double* emac_dev_)
+      : h(h_), L(L_), rel_tol(rel_tol_), max_iter(max_iter_), u_out(u_out_), emac_dev(emac_dev_),
+        mixed(h_->tsize == 4), inner_tol(mixed ? std::fmax(rel_tol_, 2e-5) : rel_tol_), max_outer(mixed ? 12 : 6),
+        f0(L_, 0.0), frel(L_, 0.0), cgrel(L_, 0.0), iters(L_, 0), steps(L_, 0), bad(L_, 0), active(L_, 1),
+        floor_hit(L_, 0) {}
 
-  for (int step = 0;; ++step) {
-    // FP64 residual of the current iterate
+  int begin(const double* emac_host) {
+    CK(cudaMemcpyAsync(emac_dev, emac_host, (size_t)L * h->ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(u_out, 0, (size_t)L * h->D * h->N * sizeof(double), h->stream));
+    std::memset(h->cg_h, 0, (size_t)L * sizeof(CgState));
+    for (int l = 0; l < L; ++l) { h->cg_h[l].active = 1; h->cg_h[l].status = ST_RUN; }
+    int rc = write_state(h, L);
+    if (rc) return rc;
+    fa = fp64_args(h, L, u_out, emac_dev, h->cg);
+    a = pass_args<T>(h, L, u_out, emac_dev);
+    return RVE_OK;
+  }
+
+  // FP64 residual of the current iterate; decide which load cases go on; for
+  // those, the inner right-hand side and the CG state.  *need = false: done.
+  int outer(bool* need) {
+    *need = false;
     CK(timed(h, K_RES, [&] { return launch_residual(fa, h->stream); }));
-    if ((rc = read_state(h, L))) return rc;
+    int rc = read_state(h, L);
+    if (rc) return rc;
     bool any = false;
     for (int l = 0; l < L; ++l) {
       if (!active[l]) continue;
@@ -658,7 +757,7 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
       }
       any = true;
     }
-    if (!any) break;
+    if (!any) return RVE_OK;
     for (int l = 0; l < L; ++l) {
       h->cg_h[l].active = active[l];
       h->cg_h[l].status = ST_RUN;
@@ -690,10 +789,14 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
       a.in = (const T*)h->fbuf;
       CK(apply_passes<T>(h, a));
     }
-    // projected CG
+    // the arguments of the projected-CG iterations
     a.cgphase = 1; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
-    if (!runner) runner.reset(new CgRunner<T>(h, L, a, check_every));
-    if ((rc = runner->run(active, (max_iter + check_every - 1) / check_every + 1))) return rc;
+    *need = true;
+    return RVE_OK;
+  }
+
+  // After the inner CG: the deferred x update, statistics, u += the correction.
+  int after_inner() {
     // apply the x update the last iteration deferred (nodal state: and u += xi)
     if (h->op_form == RVE_FORM_NODAL) {
       NodalBufs<T> nb(h, L);
@@ -701,7 +804,8 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
     } else {
       CK(timed(h, K_OTHER, [&] { return launch_cg_finish_x<T>(a, h->stream); }));
     }
-    if ((rc = read_state(h, L))) return rc;
+    int rc = read_state(h, L);
+    if (rc) return rc;
     for (int l = 0; l < L; ++l) {
       if (!active[l]) continue;
       iters[l] += h->cg_h[l].it;
@@ -718,23 +822,260 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
     for (int l = 0; l < L; ++l)
       if (bad[l]) { active[l] = 0; h->cg_h[l].active = 0; }
     if ((rc = write_state(h, L))) return rc;
+    ++step;
+    return RVE_OK;
   }
-  int worst = RVE_OK;
-  for (int l = 0; l < L; ++l) {
-    int st = RVE_OK;
-    if (bad[l]) st = RVE_ERR_NONFINITE;
-    else if (frel[l] > rel_tol && !floor_hit[l]) st = RVE_ERR_NOT_CONVERGED;
-    if (info) {
-      info[l].iterations = iters[l];
-      info[l].refine_steps = steps[l];
-      info[l].status = st;
-      info[l].reserved = 0;
-      info[l].rel_residual = frel[l];
-      info[l].cg_rel_residual = cgrel[l];
+
+  // Take every slot out of the CG kernels (a finished handle whose kernels
+  // still run in a lockstep batch graph then exits at once).
+  int deactivate() {
+    for (int l = 0; l < L; ++l) h->cg_h[l].active = 0;
+    return write_state(h, L);
+  }
+
+  int finish(rve_info* info) const {
+    int worst = RVE_OK;
+    for (int l = 0; l < L; ++l) {
+      int st = RVE_OK;
+      if (bad[l]) st = RVE_ERR_NONFINITE;
+      else if (frel[l] > rel_tol && !floor_hit[l]) st = RVE_ERR_NOT_CONVERGED;
+      if (info) {
+        info[l].iterations = iters[l];
+        info[l].refine_steps = steps[l];
+        info[l].status = st;
+        info[l].reserved = 0;
+        info[l].rel_residual = frel[l];
+        info[l].cg_rel_residual = cgrel[l];
+      }
+      if (st == RVE_ERR_NONFINITE || (st != RVE_OK && worst == RVE_OK)) worst = st;
     }
-    if (st == RVE_ERR_NONFINITE || (st != RVE_OK && worst == RVE_OK)) worst = st;
+    return worst;
   }
-  return worst;
+};
+
+constexpr int kCheckEvery = 8;  // CG iterations per graph; even: the factored form alternates its buffers
+
+template <typename T>
+int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max_iter, rve_info* info,
+               double* u_out, double* emac_dev) {
+  FeSolve<T> sv(h, L, rel_tol, max_iter, u_out, emac_dev);
+  int rc = sv.begin(emac_host);
+  if (rc) return rc;
+  std::unique_ptr<CgRunner<T>> runner;  // built at the first inner solve, reused by later ones
+  for (;;) {
+    bool need = false;
+    if ((rc = sv.outer(&need))) return rc;
+    if (!need) break;
+    if (!runner) runner.reset(new CgRunner<T>(h, L, sv.a, kCheckEvery));
+    if ((rc = runner->run(sv.active, (max_iter + kCheckEvery - 1) / kCheckEvery + 1))) return rc;
+    if ((rc = sv.after_inner())) return rc;
+  }
+  return sv.finish(info);
+}
+
+// The projected-CG iterations of several handles (the size groups of a
+// batch) as ONE CUDA graph per batch of K iterations: a fork from the batch's
+// stream to every handle's stream, K iterations of every handle on its own
+// stream (parallel branches of the graph), each branch's copy of its CG states
+// to its pinned host buffer, and a join back.  Two copies of the graph are
+// launched alternately as in CgRunner, so the host checks batch i while batch
+// i+1 runs.  Every kernel skips the slots whose CG stopped or that are not
+// active (per-RVE, per-load-case masks): a handle that has finished costs
+// only the early exits of its kernels.
+template <typename T> struct MultiRunner {
+  cudaStream_t root;
+  std::vector<rve_s*> hs;
+  std::vector<int> Ls;
+  std::vector<PassArgs<T>> as;
+  int K;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, copied[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> join;
+
+  CgState* host(int b, size_t i) { return b == 0 ? hs[i]->cg_h : hs[i]->cg_h2; }
+
+  // Fork, K iterations of every handle, state copies, join (captured or direct).
+  cudaError_t issue(int b) {
+    cudaError_t e = cudaEventRecord(fork, root);
+    for (size_t i = 0; i < hs.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(hs[i]->stream, fork, 0);
+    for (size_t i = 0; i < hs.size() && e == cudaSuccess; ++i) {
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = cg_iteration<T>(hs[i], as[i], k);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host(b, i), hs[i]->cg, (size_t)Ls[i] * sizeof(CgState), cudaMemcpyDeviceToHost,
+                            hs[i]->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(join[i], hs[i]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(root, join[i], 0);
+    }
+    return e;
+  }
+
+  MultiRunner(cudaStream_t root_, const std::vector<rve_s*>& hs_, const std::vector<int>& Ls_,
+              const std::vector<PassArgs<T>>& as_, int K_)
+      : root(root_), hs(hs_), Ls(Ls_), as(as_), K(K_), join(hs_.size(), nullptr) {
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (auto& ev : join) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (int b = 0; b < 2; ++b) cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+    for (int b = 0; b < 2; ++b) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      const cudaError_t e = issue(b);
+      const cudaError_t e2 = cudaStreamEndCapture(root, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess || !g || cudaGraphInstantiate(&exec[b], g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        exec[b] = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+      if (!exec[b]) break;
+    }
+    if (!exec[0] || !exec[1])
+      for (int b = 0; b < 2; ++b) {
+        if (exec[b]) cudaGraphExecDestroy(exec[b]);
+        exec[b] = nullptr;
+      }
+  }
+  ~MultiRunner() {
+    for (int b = 0; b < 2; ++b) {
+      if (exec[b]) cudaGraphExecDestroy(exec[b]);
+      if (copied[b]) cudaEventDestroy(copied[b]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    for (auto& ev : join)
+      if (ev) cudaEventDestroy(ev);
+  }
+  cudaError_t launch(int b) {
+    cudaError_t e = exec[b] ? cudaGraphLaunch(exec[b], root) : issue(b);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[b], root);
+    return e;
+  }
+  // Order the batch stream after the work queued on the given handles' streams.
+  int sync_in(const std::vector<size_t>& which) {
+    for (size_t i : which)
+      if (cudaEventRecord(join[i], hs[i]->stream) != cudaSuccess || cudaStreamWaitEvent(root, join[i], 0) != cudaSuccess) {
+        cudaGetLastError();
+        return RVE_ERR_CUDA;
+      }
+    return RVE_OK;
+  }
+  // ... and every handle's stream after the batch stream.
+  int sync_out() {
+    if (cudaEventRecord(fork, root) != cudaSuccess) { cudaGetLastError(); return RVE_ERR_CUDA; }
+    for (auto* h : hs)
+      if (cudaStreamWaitEvent(h->stream, fork, 0) != cudaSuccess) { cudaGetLastError(); return RVE_ERR_CUDA; }
+    return RVE_OK;
+  }
+  // No active slot of handle i is still iterating in the state copy of batch b.
+  bool idle(int b, size_t i, const std::vector<int>& active) {
+    for (int l = 0; l < Ls[i]; ++l)
+      if (active[l] && host(b, i)[l].status == ST_RUN) return false;
+    return true;
+  }
+  // Launch batches until every handle is done.  A handle whose inner solve has
+  // finished (no active slot still iterating) is handed to transition(i) at
+  // once, with no graph in flight (the copies in flight are drained first);
+  // transition() queues that handle's next refinement step (or marks it done)
+  // and the launches resume, so every handle advances on its own while all of
+  // them share one graph.  max_batches bounds the launches.
+  template <class Transition>
+  int drive(const std::vector<const std::vector<int>*>& active, std::vector<char>& done, Transition transition,
+            long max_batches) {
+    std::vector<size_t> all(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) all[i] = i;
+    if (int rc = sync_in(all)) return rc;
+    int cur = 0;
+    if (cudaError_t e = launch(cur)) return map_err(e);
+    bool other = false;   // the other copy is in flight
+    for (long n = 1;; ++n) {
+      const bool ahead = n < max_batches;
+      if (ahead) {
+        if (cudaError_t e = launch(1 - cur)) return map_err(e);
+        other = true;
+      }
+      if (cudaError_t e = cudaEventSynchronize(copied[cur])) return map_err(e);
+      std::vector<size_t> ready;
+      for (size_t i = 0; i < hs.size(); ++i)
+        if (!done[i] && idle(cur, i, *active[i])) ready.push_back(i);
+      if (ready.empty() && ahead) {
+        cur = 1 - cur;
+        continue;
+      }
+      if (other) {
+        if (cudaError_t e = cudaEventSynchronize(copied[1 - cur])) return map_err(e);
+        other = false;
+      }
+      if (int rc = sync_out()) return rc;
+      if (!ahead) return RVE_OK;   // launch budget spent: the caller finishes every handle
+      for (size_t i : ready)
+        if (int rc = transition(i)) return rc;
+      bool all_done = true;
+      for (size_t i = 0; i < hs.size(); ++i) all_done = all_done && done[i];
+      if (all_done) return RVE_OK;
+      if (int rc = sync_in(ready)) return rc;
+      cur = 0;
+      if (cudaError_t e = launch(cur)) return map_err(e);
+    }
+  }
+};
+
+// A batch solve from one host thread: every size group runs the refinement
+// phases of FeSolve, and the inner projected CG of all groups runs as one
+// graph per K iterations (MultiRunner); a group moves to its next refinement
+// step as soon as its own inner solve has finished.  emacs[g] are the
+// macroscopic strains of group g's slots; infos[g] receives their statistics
+// and codes[g] their status (the return value is an error of the whole call).
+template <typename T>
+int batch_lockstep(cudaStream_t root, const std::vector<rve_s*>& hs, const std::vector<std::vector<double>>& emacs,
+                   double rel_tol, int max_iter, std::vector<std::vector<rve_info>>& infos, std::vector<int>& codes) {
+  const size_t G = hs.size();
+  std::vector<std::unique_ptr<FeSolve<T>>> sv(G);
+  std::vector<int> Ls(G);
+  std::vector<char> done(G, 0);
+  bool any = false;
+  for (size_t g = 0; g < G; ++g) {
+    Ls[g] = (int)(emacs[g].size() / hs[g]->ns);
+    sv[g].reset(new FeSolve<T>(hs[g], Ls[g], rel_tol, max_iter, hs[g]->u, hs[g]->emac_d));
+    if (int rc = sv[g]->begin(emacs[g].data())) return rc;
+    bool need = false;
+    if (int rc = sv[g]->outer(&need)) return rc;
+    if (!need) {
+      done[g] = 1;
+      if (int rc = sv[g]->deactivate()) return rc;
+    }
+    any = any || need;
+  }
+  if (any) {
+    std::vector<PassArgs<T>> as(G);
+    std::vector<const std::vector<int>*> act(G);
+    for (size_t g = 0; g < G; ++g) {
+      as[g] = sv[g]->a;  // the CG-iteration arguments (outer() leaves them so for a group that iterates)
+      as[g].cgphase = 1; as[g].amode = A_CG; as[g].pmode = P_G; as[g].emode = E_CG;
+      act[g] = &sv[g]->active;
+    }
+    MultiRunner<T> runner(root, hs, Ls, as, kCheckEvery);
+    auto transition = [&](size_t g) -> int {
+      if (int rc = sv[g]->after_inner()) return rc;
+      bool need = false;
+      if (int rc = sv[g]->outer(&need)) return rc;
+      if (!need) {
+        done[g] = 1;
+        return sv[g]->deactivate();
+      }
+      return RVE_OK;
+    };
+    const long per_solve = (max_iter + kCheckEvery - 1) / kCheckEvery + 1;
+    const long max_batches = 1 + (long)G * 13 * per_solve;   // every group's refinement steps in turn
+    if (int rc = runner.drive(act, done, transition, max_batches)) return rc;
+    for (size_t g = 0; g < G; ++g)
+      if (!done[g])
+        if (int rc = sv[g]->after_inner()) return rc;
+  }
+  for (size_t g = 0; g < G; ++g) {
+    infos[g].resize(Ls[g]);
+    codes[g] = sv[g]->finish(infos[g].data());
+  }
+  return RVE_OK;
 }
 
 // Plain projected CG on the strain fluctuation (the scheme of Sec. 2.1 as the
@@ -1040,6 +1381,7 @@ int tangent_from_stress(int ns, const double* S, const double* emac, double* C) 
 
 struct rve_batch_s {
   int dim = 0, count = 0, precision = RVE_FP64;
+  int device = -1;              // the device current at rve_batch_create
   double nu = 0.3;
   struct Group {
     int n[3] = {1, 1, 1};
@@ -1049,6 +1391,7 @@ struct rve_batch_s {
     cudaStream_t stream = nullptr;
   };
   std::vector<Group> groups;
+  cudaStream_t root = nullptr;  // the stream the batch's CG graphs are launched on
   std::vector<int> group_of, slot_of;
   int L = 0;
   bool solved = false;
@@ -1113,6 +1456,7 @@ int rve_create(rve_t* out, int dim, const int64_t* n, const double* length, int 
 }
 
 int rve_destroy(rve_t h) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h) return RVE_OK;
   cudaStreamSynchronize(h->stream);
   flush_timing(h);
@@ -1131,6 +1475,7 @@ int rve_destroy(rve_t h) {
 }
 
 int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h) return RVE_ERR_ARG;
   if (n_voxels) *n_voxels = h->N;
   if (m) *m = h->m;
@@ -1140,6 +1485,7 @@ int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim) {
 }
 
 int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_flags) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !E || (E_dtype != RVE_F32 && E_dtype != RVE_F64)) return RVE_ERR_ARG;
   if (!(nu > -1.0 && nu < 0.5)) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
@@ -1173,6 +1519,7 @@ int rve_set_material(rve_t h, const void* E, int E_dtype, double nu, int ptr_fla
 }
 
 int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !E_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_iter < 1) return RVE_ERR_ARG;
   if (!h->has_material || h->finite) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
@@ -1180,7 +1527,7 @@ int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_ite
   h->solved = false;
   int rc = ensure_capacity(h, L);
   if (rc) return rc;
-  if (h->var[0] < 0 || h->var[1] < 0) {
+  if (h->var[0] < 0 || h->var[1] < 0 || h->var[2] < 0 || h->var[3] < 0) {
     rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
     if (rc) return rc;
   }
@@ -1199,12 +1546,14 @@ int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_ite
 }
 
 int rve_mean_stress(rve_t h, double* S) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !S || !h->solved) return RVE_ERR_ARG;
   std::memcpy(S, h->S_h.data(), h->S_h.size() * sizeof(double));
   return RVE_OK;
 }
 
 int rve_effective_tangent(rve_t h, double* C) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !C || !h->solved || h->L_solved != h->ns) return RVE_ERR_ARG;
   const int ns = h->ns;
   std::vector<double> Minv((size_t)ns * ns);
@@ -1220,6 +1569,7 @@ int rve_effective_tangent(rve_t h, double* C) {
 }
 
 int rve_energy_tangent(rve_t h, double* Ce) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !Ce || !h->solved) return RVE_ERR_ARG;
   if (h->deriv != D_FE) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
@@ -1252,6 +1602,7 @@ int rve_energy_tangent(rve_t h, double* Ce) {
 }
 
 int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !eps || !h->solved || load_case < 0 || load_case >= h->L_solved) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   Fp64Args fa = fp64_args(h, h->L_solved, h->u, h->emac_d, h->cg);
@@ -1272,6 +1623,7 @@ int rve_get_strain(rve_t h, int load_case, void* eps, int ptr_flags) {
 }
 
 int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter, void* grad_E, int ptr_flags) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !W || !grad_E || !h->solved || h->L_solved != h->ns || !(rel_tol > 0.0) || max_iter < 1)
     return RVE_ERR_ARG;
   if (h->deriv != D_FE) return RVE_ERR_ARG;
@@ -1333,6 +1685,7 @@ int rve_adjoint(rve_t h, const double* W, double rel_tol, int max_iter, void* gr
 }
 
 int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int ptr_flags) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !p || !q) return RVE_ERR_ARG;
   if (apply_material && !h->has_material) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
@@ -1364,25 +1717,26 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
 }
 
 int rve_schedule(rve_t h, int* variants, float* candidate_ms) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !variants) return RVE_ERR_ARG;
-  variants[0] = h->var[0];
-  variants[1] = h->var[1];
+  for (int w = 0; w < RVE_SCHED_PASSES; ++w) variants[w] = h->var[w];
   if (candidate_ms)
-    for (int w = 0; w < 2; ++w)
-      for (int v = 0; v < 3; ++v) candidate_ms[w * 3 + v] = h->tune_ms[w][v];
+    for (int w = 0; w < RVE_SCHED_PASSES; ++w)
+      for (int v = 0; v < RVE_SCHED_VARIANTS; ++v) candidate_ms[w * RVE_SCHED_VARIANTS + v] = h->tune_ms[w][v];
   return RVE_OK;
 }
 
 int rve_set_schedule(rve_t h, const int* variants) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !variants) return RVE_ERR_ARG;
-  for (int w = 0; w < 2; ++w)
-    if (variants[w] < -1 || variants[w] > 2) return RVE_ERR_ARG;
-  h->var[0] = variants[0];
-  h->var[1] = variants[1];
+  for (int w = 0; w < RVE_SCHED_PASSES; ++w)
+    if (variants[w] < -1 || variants[w] >= rve_sched_candidates(h, w)) return RVE_ERR_ARG;
+  for (int w = 0; w < RVE_SCHED_PASSES; ++w) h->var[w] = variants[w];
   return RVE_OK;
 }
 
 int rve_set_operator_form(rve_t h, int form) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || (form != RVE_FORM_STRESS && form != RVE_FORM_FACTORED && form != RVE_FORM_NODAL)) return RVE_ERR_ARG;
   if (form != RVE_FORM_STRESS && (h->deriv != D_FE || h->finite)) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
@@ -1398,6 +1752,7 @@ int rve_set_operator_form(rve_t h, int form) {
 }
 
 int rve_set_derivative(rve_t h, int derivative) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || derivative < RVE_DERIV_FE || derivative > RVE_DERIV_FOURIER2) return RVE_ERR_ARG;
   if (derivative != RVE_DERIV_FE && (h->precision != RVE_FP64 || h->op_form != RVE_FORM_STRESS)) return RVE_ERR_ARG;
   if (derivative == RVE_DERIV_FOURIER2 && h->dim != 2) return RVE_ERR_ARG;
@@ -1420,6 +1775,7 @@ int rve_set_derivative(rve_t h, int derivative) {
 }
 
 int rve_derivative(rve_t h, int* derivative, int* nq) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !derivative) return RVE_ERR_ARG;
   *derivative = h->deriv;
   if (nq) *nq = h->nq;
@@ -1427,6 +1783,7 @@ int rve_derivative(rve_t h, int* derivative, int* nq) {
 }
 
 int rve_set_kinematics(rve_t h, int kinematics) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || (kinematics != RVE_SMALL_STRAIN && kinematics != RVE_FINITE_STRAIN)) return RVE_ERR_ARG;
   const bool fin = kinematics == RVE_FINITE_STRAIN;
   if (fin && (h->precision != RVE_FP64 || h->op_form != RVE_FORM_STRESS || h->deriv != D_FE)) return RVE_ERR_ARG;
@@ -1440,13 +1797,14 @@ int rve_set_kinematics(rve_t h, int kinematics) {
   }
   h->finite = fin ? 1 : 0;
   h->m = fin ? (h->dim == 2 ? 9 : 54) : h->ns * h->nq;
-  if (h->var[0] < 0) h->var[0] = 0;
-  if (h->var[1] < 0) h->var[1] = 0;
+  for (int w = 0; w < RVE_SCHED_PASSES; ++w)
+    if (h->var[w] < 0) h->var[w] = 0;
   return ensure_capacity(h, 1);
 }
 
 int rve_solve_finite(rve_t h, const double* F_macro, int L, double rel_tol, int max_newton, int max_iter,
                      rve_info* info) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !F_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_newton < 0 || max_iter < 1) return RVE_ERR_ARG;
   if (!h->has_material || !h->finite) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
@@ -1464,12 +1822,14 @@ int rve_solve_finite(rve_t h, const double* F_macro, int L, double rel_tol, int 
 }
 
 int rve_mean_piola(rve_t h, double* P) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !P || !h->solved || !h->finite) return RVE_ERR_ARG;
   std::memcpy(P, h->P_h.data(), h->P_h.size() * sizeof(double));
   return RVE_OK;
 }
 
 int rve_get_deformation(rve_t h, int load_case, void* F, int ptr_flags) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !F || !h->solved || !h->finite || load_case < 0 || load_case >= h->L_solved) return RVE_ERR_ARG;
   if (int jr = join_user(h)) return jr;
   const int nq = h->dim == 2 ? 2 : 6;
@@ -1481,12 +1841,14 @@ int rve_get_deformation(rve_t h, int load_case, void* F, int ptr_flags) {
 }
 
 int rve_operator_form(rve_t h, int* form) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !form) return RVE_ERR_ARG;
   *form = h->op_form;
   return RVE_OK;
 }
 
 int rve_timing_enable(rve_t h, int enable) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h) return RVE_ERR_ARG;
   CK(cudaStreamSynchronize(h->stream));
   flush_timing(h);
@@ -1495,6 +1857,7 @@ int rve_timing_enable(rve_t h, int enable) {
 }
 
 int rve_timing_read(rve_t h, double* ms, int64_t* launches) {
+  DeviceScope dev_scope(h ? h->device : -1);
   if (!h || !ms || !launches) return RVE_ERR_ARG;
   CK(cudaStreamSynchronize(h->stream));
   flush_timing(h);
@@ -1508,11 +1871,14 @@ int rve_timing_read(rve_t h, double* ms, int64_t* launches) {
 }
 
 int rve_batch_destroy(rve_batch_t b) {
+  DeviceScope dev_scope(b ? b->device : -1);
   if (!b) return RVE_OK;
+  if (b->root) cudaStreamSynchronize(b->root);
   for (auto& g : b->groups) {
     if (g.h) rve_destroy(g.h);
     if (g.stream) cudaStreamDestroy(g.stream);
   }
+  if (b->root) cudaStreamDestroy(b->root);
   delete b;
   return RVE_OK;
 }
@@ -1524,6 +1890,7 @@ int rve_batch_create(rve_batch_t* out, int dim, int count, const int64_t* n, int
   rve_batch_s* b = new (std::nothrow) rve_batch_s();
   if (!b) return RVE_ERR_OOM;
   b->dim = dim; b->count = count; b->precision = precision; b->nu = nu;
+  if (cudaGetDevice(&b->device) != cudaSuccess) { cudaGetLastError(); delete b; return RVE_ERR_CUDA; }
   b->group_of.assign(count, -1);
   b->slot_of.assign(count, -1);
   std::map<std::vector<int64_t>, int> index;
@@ -1543,6 +1910,9 @@ int rve_batch_create(rve_batch_t* out, int dim, int count, const int64_t* n, int
     b->slot_of[i] = (int)b->groups[gi].members.size();
     b->groups[gi].members.push_back(i);
   }
+  if (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError(); rve_batch_destroy(b); return RVE_ERR_CUDA;
+  }
   for (auto& g : b->groups) {
     g.has_mat.assign(g.members.size(), 0);
     if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1559,6 +1929,7 @@ int rve_batch_create(rve_batch_t* out, int dim, int count, const int64_t* n, int
 }
 
 int rve_batch_set_material(rve_batch_t b, int index, const void* E, int E_dtype, int ptr_flags) {
+  DeviceScope dev_scope(b ? b->device : -1);
   if (!b || !E || index < 0 || index >= b->count || (E_dtype != RVE_F32 && E_dtype != RVE_F64)) return RVE_ERR_ARG;
   auto& g = b->groups[b->group_of[index]];
   std::vector<double> e64;
@@ -1572,6 +1943,7 @@ int rve_batch_set_material(rve_batch_t b, int index, const void* E, int E_dtype,
 }
 
 int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol, int max_iter, rve_info* info) {
+  DeviceScope dev_scope(b ? b->device : -1);
   if (!b || !E_macro || L < 1 || L > 64 || !(rel_tol > 0.0) || max_iter < 1) return RVE_ERR_ARG;
   const int ns = b->dim == 2 ? 3 : 6;
   for (int i = 0; i < L * ns; ++i) if (!std::isfinite(E_macro[i])) return RVE_ERR_ARG;
@@ -1581,41 +1953,39 @@ int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol,
   const int G = (int)b->groups.size();
   std::vector<int> codes(G, RVE_OK);
   std::vector<std::vector<rve_info>> infos(G);
-  // one host thread per group: the groups' launches overlap on their streams
-  auto run = [&](int gi) {
+  std::vector<std::vector<double>> emacs(G);
+  std::vector<rve_s*> hs(G);
+  for (int gi = 0; gi < G; ++gi) {
     auto& g = b->groups[gi];
     rve_s* h = g.h;
+    hs[gi] = h;
     const int Lg = (int)g.members.size() * L;
-    std::vector<double> em((size_t)Lg * ns);
+    emacs[gi].resize((size_t)Lg * ns);
     for (int s = 0; s < Lg; ++s)
-      for (int c = 0; c < ns; ++c) em[(size_t)s * ns + c] = E_macro[(size_t)(s % L) * ns + c];
+      for (int c = 0; c < ns; ++c) emacs[gi][(size_t)s * ns + c] = E_macro[(size_t)(s % L) * ns + c];
     h->lcs = L;
     h->has_material = true;
     h->solved = false;
     int rc = ensure_capacity(h, Lg);
-    if (rc) { codes[gi] = rc; return; }
-    if (h->var[0] < 0 || h->var[1] < 0) {
+    if (rc) return rc;
+    if (h->var[0] < 0 || h->var[1] < 0 || h->var[2] < 0 || h->var[3] < 0) {
       rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
-      if (rc) { codes[gi] = rc; return; }
+      if (rc) return rc;
     }
-    infos[gi].resize(Lg);
-    const int st = (h->precision == RVE_MIXED)
-                       ? solve_impl<float>(h, em.data(), Lg, rel_tol, max_iter, infos[gi].data(), h->u, h->emac_d)
-                       : solve_impl<double>(h, em.data(), Lg, rel_tol, max_iter, infos[gi].data(), h->u, h->emac_d);
-    if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED && st != RVE_ERR_NONFINITE) { codes[gi] = st; return; }
-    h->emac_h = em;
-    h->L_solved = Lg;
-    rc = compute_mean_stress(h, Lg);
-    if (rc) { codes[gi] = rc; return; }
+  }
+  // every group's refinement in lockstep, the CG iterations of all groups in one graph
+  const int rcl = (b->precision == RVE_MIXED) ? batch_lockstep<float>(b->root, hs, emacs, rel_tol, max_iter, infos, codes)
+                                              : batch_lockstep<double>(b->root, hs, emacs, rel_tol, max_iter, infos, codes);
+  if (rcl) return rcl;
+  for (int gi = 0; gi < G; ++gi) {
+    rve_s* h = hs[gi];
+    const int st = codes[gi];
+    if (st != RVE_OK && st != RVE_ERR_NOT_CONVERGED && st != RVE_ERR_NONFINITE) return st;
+    h->emac_h = emacs[gi];
+    h->L_solved = (int)infos[gi].size();
+    int rc = compute_mean_stress(h, h->L_solved);
+    if (rc) return rc;
     h->solved = true;
-    codes[gi] = st;
-  };
-  if (G == 1) {
-    run(0);
-  } else {
-    std::vector<std::thread> th;
-    for (int gi = 0; gi < G; ++gi) th.emplace_back(run, gi);
-    for (auto& t : th) t.join();
   }
   int worst = RVE_OK;
   for (int gi = 0; gi < G; ++gi) {
@@ -1635,6 +2005,7 @@ int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol,
 }
 
 int rve_batch_mean_stress(rve_batch_t b, int index, double* S) {
+  DeviceScope dev_scope(b ? b->device : -1);
   if (!b || !S || !b->solved || index < 0 || index >= b->count) return RVE_ERR_ARG;
   const int ns = b->dim == 2 ? 3 : 6;
   const auto& g = b->groups[b->group_of[index]];
@@ -1643,6 +2014,7 @@ int rve_batch_mean_stress(rve_batch_t b, int index, double* S) {
 }
 
 int rve_batch_effective_tangent(rve_batch_t b, int index, double* C) {
+  DeviceScope dev_scope(b ? b->device : -1);
   const int ns = b ? (b->dim == 2 ? 3 : 6) : 0;
   if (!b || !C || !b->solved || b->L != ns) return RVE_ERR_ARG;
   std::vector<double> S((size_t)ns * ns);

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "device_once.h"
+
 namespace rve {
 
 // ---------------------------------------------------------------- complex
@@ -105,10 +107,16 @@ __device__ __forceinline__ void fft_reg(C* v) {
   }
 }
 
-// Four-step split N = N1 * N2 with N1 <= N2 <= 32.
-template <int N> struct FftSplit {
-  static constexpr int N1 = (N <= 16) ? 4 : (N == 32) ? 4 : (N == 64) ? 8 : (N == 128) ? 8
-                          : (N == 256) ? 16 : (N == 512) ? 16 : 32;
+// Four-step split N = N1 * N2 with N1 <= N2 <= 32 (the radix schedule of one
+// transform).  Variant 0 is the most square split; variant 1 halves N1 and
+// doubles N2 where N2 stays within the 32-point register FFT (16 = 2 x 8,
+// 32 = 2 x 16, 64 = 4 x 16, 128 = 4 x 32, 256 = 8 x 32) and is variant 0
+// otherwise (512, 1024).  The autotuner picks one per axis.
+template <int N, int V = 0> struct FftSplit {
+  static constexpr int N1_0 = (N <= 16) ? 4 : (N == 32) ? 4 : (N == 64) ? 8 : (N == 128) ? 8
+                            : (N == 256) ? 16 : (N == 512) ? 16 : 32;
+  static constexpr bool ALT = (V == 1) && 2 * (N / N1_0) <= 32;
+  static constexpr int N1 = ALT ? N1_0 / 2 : N1_0;
   static constexpr int N2 = N / N1;
   // leading dimension of one transform in shared memory (room for the padded
   // transpose of the middle step)
@@ -118,10 +126,31 @@ template <int N> struct FftSplit {
   static constexpr int LDO = N + N2 + 1;
 };
 
+// True when the work items of every transform, in both steps of the
+// four-step FFT below, belong to one warp: a square split (N1 = N2, so both
+// steps give transform b the items b*N1 .. b*N1 + N1 - 1), items ordered
+// transform-major in both steps, N1 dividing the warp and NT a whole number
+// of warps.  The barriers between the steps then only have to order the
+// threads of one warp (__syncwarp orders their shared-memory accesses too).
+template <int N, int NT, bool B1_FAST = false, bool B2_FAST = false, int V = 0>
+__host__ __device__ constexpr bool warp_local_fft() {
+  return FftSplit<N, V>::N1 == FftSplit<N, V>::N2 && !B1_FAST && !B2_FAST && 32 % FftSplit<N, V>::N1 == 0 &&
+         NT % 32 == 0;
+}
+
+// Number of distinct splits of a length (1 or 2).
+template <int N> __host__ __device__ constexpr int fft_split_count() { return FftSplit<N, 1>::ALT ? 2 : 1; }
+
+// Barrier between two steps of a transform: warp-level when LOCAL.
+template <bool LOCAL> __device__ __forceinline__ void fft_step_sync() {
+  if constexpr (LOCAL) __syncwarp();
+  else __syncthreads();
+}
+
 // Threads that give one work item per thread in both steps for NB transforms,
 // within [128, 1024], a multiple of 32.
-template <int N, int NB> constexpr int fft_threads() {
-  constexpr int w = NB * FftSplit<N>::N2;
+template <int N, int NB, int V = 0> constexpr int fft_threads() {
+  constexpr int w = NB * FftSplit<N, V>::N2;
   constexpr int t = w < 128 ? 128 : (w > 1024 ? 1024 : w);
   return (t + 31) / 32 * 32;
 }
@@ -133,11 +162,14 @@ template <int N, int NB> constexpr int fft_threads() {
 //           stride (N1 + 1) so that both access patterns are conflict-free;
 //   step 2: for every (b, k2): FFT over n1 in registers, store X[k2 + N2 k1].
 // tw[t] = exp(-2 pi i t / N) (host FP64 libm, rounded to T).  The caller must
-// __syncthreads() before; the function ends with a barrier.
+// __syncthreads() before; the function ends with a barrier.  Every step reads
+// and writes only its own transform's row, so with a square split the
+// barriers inside are warp-level (warp_local_fft).
 template <typename T, int N, int NB, int LD, int NT, int S>
 __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
+  constexpr bool LOCAL = warp_local_fft<N, NT>();
   static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
   constexpr int W1 = NB * N1, W2 = NB * N2;
   constexpr int I1 = (W1 + NT - 1) / NT, I2 = (W2 + NT - 1) / NT;
@@ -153,7 +185,7 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
         for (int n2 = 0; n2 < N2; ++n2) v[i][n2] = src[n2 * N1];
       }
     }
-    __syncthreads();
+    fft_step_sync<LOCAL>();
 #pragma unroll
     for (int i = 0; i < I1; ++i) {
       const int it = threadIdx.x + i * NT;
@@ -174,7 +206,7 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
       }
     }
   }
-  __syncthreads();
+  fft_step_sync<LOCAL>();
   {
     C v[I2][N1];
 #pragma unroll
@@ -187,7 +219,7 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
         for (int n1 = 0; n1 < N1; ++n1) v[i][n1] = src[n1];
       }
     }
-    __syncthreads();
+    fft_step_sync<LOCAL>();
 #pragma unroll
     for (int i = 0; i < I2; ++i) {
       const int it = threadIdx.x + i * NT;
@@ -214,11 +246,17 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
 //   layout the load / store touches;
 //   BATCH_STORE: store.batch(b, k2, v) receives the N1 outputs of an item at
 //   once (k = k2 + N2 k1), so that it can issue all of its global loads first.
+// A load() or store() that touches buf touches only transform b's own row
+// (b*LD .. b*LD + LD - 1); so with a square split the barriers between the
+// steps are warp-level (warp_local_fft) and only the final STORE_SMEM barrier,
+// after which the caller reads across transforms, is block-wide.
+// V selects the split (FftSplit<N, V>).
 template <typename T, int N, int NB, int LD, int NT, int S, bool LOAD_SMEM, bool STORE_SMEM, bool B1_FAST,
-          bool B2_FAST, class Load, class Store, bool BATCH_STORE = false>
+          bool B2_FAST, int V = 0, class Load, class Store, bool BATCH_STORE = false>
 __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ tw, Load load, Store store) {
   using C = cplx<T>;
-  constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
+  constexpr int N1 = FftSplit<N, V>::N1, N2 = FftSplit<N, V>::N2;
+  constexpr bool LOCAL = warp_local_fft<N, NT, B1_FAST, B2_FAST, V>();
   static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
   constexpr int W1 = NB * N1, W2 = NB * N2;
   constexpr int I1 = (W1 + NT - 1) / NT, I2 = (W2 + NT - 1) / NT;
@@ -233,7 +271,7 @@ __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ t
         for (int n2 = 0; n2 < N2; ++n2) v[i][n2] = load(b, n1 + N1 * n2);
       }
     }
-    if (LOAD_SMEM) __syncthreads();
+    if (LOAD_SMEM) fft_step_sync<LOCAL>();
 #pragma unroll
     for (int i = 0; i < I1; ++i) {
       const int it = threadIdx.x + i * NT;
@@ -254,7 +292,7 @@ __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ t
       }
     }
   }
-  __syncthreads();
+  fft_step_sync<LOCAL>();
   {
     C v[I2][N1];
 #pragma unroll
@@ -267,7 +305,7 @@ __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ t
         for (int n1 = 0; n1 < N1; ++n1) v[i][n1] = src[n1];
       }
     }
-    if (STORE_SMEM) __syncthreads();
+    if (STORE_SMEM) fft_step_sync<LOCAL>();
 #pragma unroll
     for (int i = 0; i < I2; ++i) {
       const int it = threadIdx.x + i * NT;
@@ -363,6 +401,17 @@ template <typename T, int VL> __device__ __forceinline__ void vstoren(T* d, cons
 template <typename K> inline void set_smem_attrs(K kernel, size_t smem) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
+// The calling thread's current device, or -1 if it cannot be read (then a
+// DeviceOnce set-up runs on every call).
+inline int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return d;
 }
 
 // ------------------------------------------------------------ reductions

@@ -64,7 +64,8 @@ template <typename T> struct PassArgs {
   int part_stride;
   int amode, emode, pmode;
   int cgphase;       // 1 inside the CG loop: passes skip load cases whose CG stopped
-  int var_a, var_e;  // tile variants of passes A and E: 0 default rows per block, 1 half, 2 double
+  int var_a, var_e;  // tile variants of passes A (0..4) and E (0..2): see the launchers
+  int var_c, var_y;  // FFT split variants (FftSplit<N, V>) of pass C's axis and of passes B / D (3D)
   int comp_in;       // number of components in the spectrum for this pass (m or D)
   int deriv;         // Deriv
 };

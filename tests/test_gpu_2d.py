@@ -176,14 +176,40 @@ def test_every_tile_variant_gives_the_same_solution(dim):
                 code, info = r.solve(np.eye(ns), rel_tol=1e-11, max_iter=3000)
                 assert code == 0, info
                 Cs.append(r.effective_tangent())
-                assert r.schedule()[0] == [va, ve]
+                assert r.schedule()[0] == [va, ve, 0, 0]
     for C in Cs[1:]:
         assert rel_max(C, Cs[0]) < 1e-10
     with RVE(n, precision="mixed") as r:
         r.set_material(E, 0.3)
         r.solve(np.eye(ns), rel_tol=1e-11, max_iter=3000)
         var, ms = r.schedule()
-        assert all(v in (0, 1, 2) for v in var)
+        assert var[0] in range(5) and var[1] in range(3) and var[2] in (0, 1) and var[3] in (0, 1)
+        # candidate times are those of the last tuning of this handle (zero when the
+        # choice came from the per-grid cache of an earlier handle)
+        assert len(ms) == 4 and all(len(m) == 5 and min(m) >= 0 for m in ms)
+
+
+@pytest.mark.parametrize("n", [(64, 64), (64, 32, 16), (16, 128, 64)])
+def test_every_fft_schedule_gives_the_same_operator(n):
+    """The autotuner may pick any split of the four-step FFTs (pass C's axis,
+    the y axis of passes B / D) and any thread variant of pass A: every
+    schedule must apply the same operator q = G C p (FP32, to 2e-5 of the
+    oracle's field maximum)."""
+    from paper_2105_03297_gb300 import RVE
+    dim = len(n)
+    E = lognormal(n, 62)
+    P = Problem(n, E, 0.3)
+    p = np.random.default_rng(63).standard_normal((P.m,) + E.shape).astype(np.float32).astype(np.float64)
+    ref = P.operator(p)
+    scheds = [(a, 0, c, y) for a in range(5 if n[0] >= 64 else 3)
+              for c in (0, 1) for y in ((0, 1) if dim == 3 else (0,))]
+    with RVE(n, precision="mixed") as r:
+        r.set_material(E, 0.3)
+        for sch in scheds:
+            r.set_schedule(*sch)
+            assert r.schedule()[0] == list(sch)
+            q = r.apply_operator(p.reshape(P.m, -1)).reshape(ref.shape)
+            assert np.abs(q - ref).max() <= 2e-5 * np.abs(ref).max(), sch
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

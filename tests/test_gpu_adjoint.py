@@ -4,9 +4,11 @@ on the 64^3 log-normal workload (16 seeded voxels).
 
 J = C_1111 is differenced in its energy form (second order in the solve
 error).  One voxel changes J by about 2 h E_v g_v ~ 1e-11 at h = 1e-6 while J
-is about 1.7, so FP64 cancellation limits the h = 1e-6 difference to about
-1e-4 relative; h = 1e-3 (truncation ~h^2) is checked to 1e-5.  The 1e-9 bar
-applies to the oracle's adjoint (golden file).
+is about 1.7, so FP64 rounding of the two solves' J (a few 1e-15 relative)
+limits the h = 1e-6 difference to a few 1e-4 relative; the error falls as 1/h
+(measured on a GB300: 2.1e-4 at h = 1e-6, 4.0e-5 at 1e-5, 5.5e-6 at 1e-4), and
+h = 1e-3 (truncation ~h^2) is checked to 1e-5.  The 1e-9 bar applies to the
+oracle's adjoint (golden file).
 """
 import json
 import os
@@ -43,7 +45,7 @@ def test_autograd_matches_oracle_adjoint(prec):
     assert rel_max(Et.grad.cpu().numpy(), g_ref) < 1e-9
 
 
-@pytest.mark.parametrize("h,tol", [(1e-6, 2e-3), (1e-3, 1e-5)])
+@pytest.mark.parametrize("h,tol", [(1e-6, 5e-4), (1e-3, 1e-5)])
 def test_adjoint_vs_central_differences_lognormal64(h, tol):
     path = os.path.join(GOLDEN, "lognormal64.json")
     if not os.path.exists(path):

@@ -66,3 +66,31 @@ def test_batch_matches_single_solves():
         b.solve(np.eye(3), rel_tol=1e-11, max_iter=4000)
         for i in range(2):
             assert rel_max(b.effective_tangent(i), singles[i]) < 1e-10
+
+
+def test_uneven_batch_sides_64_to_512_against_stored_oracle():
+    """One RVE of each side of the 64-RVE uneven batch (64^2, 128^2, 256^2 and
+    512^2, thresholded Gaussian fields, contrast 10..1000), solved together as
+    one batch in mixed precision: every tangent against the oracle's stored
+    tangent to 1e-9."""
+    import json
+    import os
+    import microstructures as ms
+    from paper_2105_03297_gb300 import RVEBatch
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch4.json")
+    if not os.path.exists(path):
+        pytest.skip("golden not generated")
+    ref = json.load(open(path))
+    batch = ms.uneven_batch_2d(64, seed=1004)
+    rves = ref["rves"]
+    sizes = [tuple(r["n"]) for r in rves]
+    assert sorted(s[0] for s in sizes) == [64, 128, 256, 512]
+    with RVEBatch(sizes, precision="mixed", nu=ref["nu"]) as b:
+        for i, r in enumerate(rves):
+            n, E = batch[r["index"]]
+            assert tuple(n) == tuple(r["n"])
+            b.set_material(i, E)
+        code, info = b.solve(np.eye(3), rel_tol=1e-11, max_iter=20000)
+        assert code == 0, info
+        for i, r in enumerate(rves):
+            assert rel_max(b.effective_tangent(i), np.array(r["C_eff"])) < 1e-9, r["n"]

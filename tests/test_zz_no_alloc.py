@@ -4,10 +4,15 @@ rve_apply_operator_2d_static serves callers that cannot call cudaMalloc (an
 application owning the whole device pool through its own allocator, or a
 latency-critical loop).  It must give the same q = G C p (and the bare
 projection) as rve_apply_operator on an FP32 (mixed) handle, on consecutive
-calls that share its static scratch.  This file is collected last so that a
-run stopping at the first failure has run every other test already.
+calls that share its static scratch, and after its first call on a device it
+must take no device memory at all.  This file is collected last so that a run
+stopping at the first failure has run every other test already.
 """
 import ctypes as C
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -62,3 +67,49 @@ def test_static_operator_rejects_grids_beyond_its_scratch():
     q_dev = torch.zeros_like(p_dev)
     assert _static_apply(lib, n, E_dev, 0.3, p_dev, q_dev, True) == _rve.RVE_ERR_SCRATCH_LIMIT
     assert b"static scratch" in lib.rve_error_string(_rve.RVE_ERR_SCRATCH_LIMIT)
+
+
+# Run in a child process so that the library's first use in that process is the
+# static entry point itself: with lazy module loading the first call loads the
+# library's device code (and with it the static scratch array) into the
+# context, which is the one allocation a caller of this entry point has to
+# make at set-up time.  After it, a call must leave the free device memory
+# unchanged.
+CHILD = r"""
+import ctypes as C, json, sys
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2105_03297_gb300 import _rve
+n = (128, 64)
+N = n[0] * n[1]
+g = torch.Generator(device="cuda").manual_seed(5)
+E = torch.rand(N, device="cuda", generator=g) + 0.5
+p = torch.randn(6 * N, device="cuda", generator=g)
+q1, q2 = torch.empty_like(p), torch.empty_like(p)
+lib = _rve.load()
+torch.cuda.synchronize()
+f0 = torch.cuda.mem_get_info()[0]
+nn = (C.c_int64 * 2)(*n)
+s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+args = lambda q: (nn, None, C.c_void_p(E.data_ptr()), 0.3, C.c_void_p(p.data_ptr()), C.c_void_p(q.data_ptr()), 1, s)
+rc1 = lib.rve_apply_operator_2d_static(*args(q1))
+torch.cuda.synchronize()
+f1 = torch.cuda.mem_get_info()[0]
+rc2 = lib.rve_apply_operator_2d_static(*args(q2))
+torch.cuda.synchronize()
+f2 = torch.cuda.mem_get_info()[0]
+print(json.dumps(dict(rc1=rc1, rc2=rc2, f0=f0, f1=f1, f2=f2, same=bool(torch.equal(q1, q2)),
+                      finite=bool(torch.isfinite(q1).all()))))
+"""
+
+
+def test_static_operator_takes_no_memory_after_its_first_call():
+    require_gpu()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", CHILD, root], capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    assert d["rc1"] == 0 and d["rc2"] == 0
+    assert d["finite"] and d["same"]                 # same inputs, same scratch use: identical results
+    assert d["f2"] == d["f1"], d                     # the second call took no device memory
+    assert 0 <= d["f0"] - d["f1"] <= 256 << 20, d    # the first call: at most the library's module load
