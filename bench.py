@@ -39,6 +39,9 @@ WORKLOADS = {
     "batch64": ("batch64", "mixed", 1e-10),
     "lognormal256": ("lognormal256", "mixed", 1e-10),
     "lognormal256_fp64": ("lognormal256", "fp64", 1e-10),
+    # profiling sizes: the 256-point transforms of the 256^3 workload on a few GB
+    "lognormal256x256x32": ("lognormal256x256x32", "mixed", 1e-10),
+    "lognormal32x32x256": ("lognormal32x32x256", "mixed", 1e-10),
 }
 
 

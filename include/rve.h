@@ -173,7 +173,12 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  * variants[RVE_SCHED_PASSES] holds
  *  [0] the first pass (material + x FFT): 0 default rows per block, 1 half,
  *      2 double; with n_x >= 64 also 3 default rows and 4 half rows with one
- *      thread per 16-byte load unit of the tile;
+ *      thread per 16-byte load unit of the tile; in 3D with RVE_MIXED and
+ *      n_x >= 128 also 5, a persistent pipelined pass whose next tile's rows
+ *      arrive by bulk copies while the current tile is transformed (CG
+ *      iterations of up to 64 load cases; otherwise it runs as 0).  A bounded
+ *      device-side wait of that pass that gives up makes the solve return
+ *      RVE_ERR_TIMEOUT;
  *  [1] the last pass (inverse x FFT + CG update): 0 default rows, 1 half, 2 double;
  *  [2] the split N = N1 * N2 of the four-step FFT along the last axis (y in
  *      2D, z in 3D; the pass that applies the projection): 0 the most square
@@ -186,7 +191,7 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  * rve_schedule also returns the measured candidate times
  * candidate_ms[RVE_SCHED_PASSES][RVE_SCHED_VARIANTS] (0 where a candidate does
  * not exist or was not timed; may be NULL). */
-enum { RVE_SCHED_PASSES = 4, RVE_SCHED_VARIANTS = 5 };
+enum { RVE_SCHED_PASSES = 4, RVE_SCHED_VARIANTS = 6 };
 int rve_schedule(rve_t h, int* variants, float* candidate_ms);
 int rve_set_schedule(rve_t h, const int* variants);
 

@@ -230,4 +230,12 @@ def config_inputs(name):
         n = (256, 256, 256)
         return dict(n=n, E=lognormal_field(n, 0.0, 1.0, seed=1006), nu=0.3,
                     E_macro=unit_load_cases(3)[:1])
+    if name == "lognormal256x256x32":   # profiling size with the 256-point x and y transforms
+        n = (256, 256, 32)
+        return dict(n=n, E=lognormal_field(n, 0.0, 1.0, seed=1011), nu=0.3,
+                    E_macro=unit_load_cases(3)[:1])
+    if name == "lognormal32x32x256":    # profiling size with the 256-point z transform (pass C)
+        n = (32, 32, 256)
+        return dict(n=n, E=lognormal_field(n, 0.0, 1.0, seed=1012), nu=0.3,
+                    E_macro=unit_load_cases(3)[:1])
     raise KeyError(name)

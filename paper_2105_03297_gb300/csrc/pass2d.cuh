@@ -34,7 +34,8 @@ __device__ __forceinline__ void finish_alpha(CgState* cg, double pq) {
 __device__ __forceinline__ void finish_rr(CgState* cg, double rr, bool init) {
   if (init) {
     cg->rr0 = rr; cg->rr = rr; cg->it = 0; cg->beta = 0.0;
-    cg->status = !isfinite(rr) ? ST_BAD : (rr == 0.0 ? ST_CONV : ST_RUN);
+    // a held slot (ST_HOLD) stays held until the host releases it
+    cg->status = !isfinite(rr) ? ST_BAD : (rr == 0.0 ? ST_CONV : (cg->status == ST_HOLD ? ST_HOLD : ST_RUN));
   } else {
     cg->it += 1;
     if (!isfinite(rr)) { cg->status = ST_BAD; }
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(NT, pass_a2_min_blocks<T, NT>()) pass_a_2d(Pas
   constexpr int NP = TY / 2;
   constexpr int GS = 3;
   constexpr int KX = NX / 2 + 1;
-  constexpr int LD = FftSplit<NX>::LD;
+  constexpr int LD = ae_ld<NX>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [GS][NP][LD]
   __shared__ double red[NT / 32];
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 2 : 1) pas
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
   constexpr int GE = 3;
-  constexpr int LD = FftSplit<NX>::LD;
+  constexpr int LD = ae_ld<NX>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [GE][NP][LD]
   __shared__ double red[NT / 32];
@@ -618,7 +619,7 @@ cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NF = fft_threads<NX, 3 * (TY / 2)>();
   constexpr int NU = ((TY / 2) * (NX / Vec16<T>::n) + 31) / 32 * 32;   // load units of a tile
   constexpr int NT = (BY_UNITS && NU > NF && NU <= 1024) ? NU : NF;
-  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
+  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * ae_ld<NX>();
   auto k = pass_a_2d<T, NX, TY, NT>;
   static DeviceOnce attr;
   attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
@@ -629,7 +630,7 @@ cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
 template <typename T, int NX, int TY>
 cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 3 * (TY / 2)>();
-  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * FftSplit<NX>::LD;
+  const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * ae_ld<NX>();
   auto k = pass_e_2d<T, NX, TY, NT>;
   static DeviceOnce attr;
   attr.run(current_device(), [&] { set_smem_attrs(k, sm); });

@@ -12,6 +12,7 @@
 //      deferred to the next pass A, as in 2D).
 #pragma once
 #include "pass2d.cuh"
+#include "pass3d_pipe.cuh"
 
 namespace rve {
 
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(NT, pass_a_min_blocks<T, NT>()) pass_a_3d(Pass
   constexpr int NP = TY / 2;
   constexpr int GS = 6;
   constexpr int KX = NX / 2 + 1;
-  constexpr int LD = FftSplit<NX>::LD;
+  constexpr int LD = ae_ld<NX>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [GS][NP][LD]
   __shared__ double red[NT / 32];
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
   constexpr int NP = TY / 2;
   constexpr int KX = NX / 2 + 1;
   constexpr int GE = 6;
-  constexpr int LD = FftSplit<NX>::LD;
+  constexpr int LD = ae_ld<NX>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [GE][NP][LD]
   __shared__ double red[NT / 32];
@@ -552,7 +553,7 @@ cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NF = fft_threads<NX, 6 * (TY / 2)>();
   constexpr int NU = (pass_a_units3<T, NX, TY>() + 31) / 32 * 32;
   constexpr int NT = BY_UNITS ? (max_i<NF, NU>() > 1024 ? NF : max_i<NF, NU>()) : NF;
-  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
+  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * ae_ld<NX>();
   auto k = pass_a_3d<T, NX, TY, NT>;
   static DeviceOnce attr;
   attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
@@ -563,7 +564,7 @@ cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s) {
 template <typename T, int NX, int TY>
 cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
-  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * FftSplit<NX>::LD;
+  const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * ae_ld<NX>();
   auto k = pass_e_3d<T, NX, TY, NT>;
   static DeviceOnce attr;
   attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
@@ -572,9 +573,14 @@ cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 // Tile variants of pass A: 0 default rows per block, 1 half, 2 double (threads
-// = the FFT's); 3 default rows and 4 half rows with one thread per load unit.
+// = the FFT's); 3 default rows and 4 half rows with one thread per load unit;
+// 5 (FP32, n_x >= 128, CG iterations) the pipelined persistent pass with
+// bulk-copied rows (pass3d_pipe.cuh); other modes of variant 5 use variant 0.
 template <typename T, int NX>
 cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && NX >= 128) {
+    if (a.var_a == 5 && a.amode == A_CG && a.L <= kPipeMaxL && a.n[1] >= 4) return launch_a_3d_pipe<NX>(a, s);
+  }
   if constexpr (NX >= 64) {
     if (a.var_a == 1) return launch_a_3d_t<T, NX, tile_rows3<T>(1)>(a, s);
     if (a.var_a == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_a_3d_t<T, NX, tile_rows3<T>(2)>(a, s);

@@ -496,7 +496,7 @@ int split_count(int n) {
 // Number of candidates of schedule entry `which` for a handle.
 int rve_sched_candidates(const rve_s* h, int which) {
   switch (which) {
-    case 0: return h->n[0] >= 64 ? 5 : 3;
+    case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 6 : h->n[0] >= 64 ? 5 : 3;
     case 1: return 3;
     case 2: return split_count(h->n[h->dim - 1]);
     default: return h->dim == 3 ? split_count(h->n[1]) : 1;
@@ -704,7 +704,7 @@ template <typename T> struct FeSolve {
   int max_outer;
   int step = 0;
   std::vector<double> f0, frel, cgrel;
-  std::vector<int> iters, steps, bad, active, floor_hit;
+  std::vector<int> iters, steps, bad, active, floor_hit, timeout;
   Fp64Args fa;
   PassArgs<T> a;
 
@@ -712,7 +712,7 @@ template <typename T> struct FeSolve {
       : h(h_), L(L_), rel_tol(rel_tol_), max_iter(max_iter_), u_out(u_out_), emac_dev(emac_dev_),
         mixed(h_->tsize == 4), inner_tol(mixed ? std::fmax(rel_tol_, 2e-5) : rel_tol_), max_outer(mixed ? 12 : 6),
         f0(L_, 0.0), frel(L_, 0.0), cgrel(L_, 0.0), iters(L_, 0), steps(L_, 0), bad(L_, 0), active(L_, 1),
-        floor_hit(L_, 0) {}
+        floor_hit(L_, 0), timeout(L_, 0) {}
 
   int begin(const double* emac_host) {
     CK(cudaMemcpyAsync(emac_dev, emac_host, (size_t)L * h->ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -728,7 +728,9 @@ template <typename T> struct FeSolve {
 
   // FP64 residual of the current iterate; decide which load cases go on; for
   // those, the inner right-hand side and the CG state.  *need = false: done.
-  int outer(bool* need) {
+  // hold: the slots that go on are left held (ST_HOLD) for the caller to
+  // release, instead of running.
+  int outer(bool* need, bool hold = false) {
     *need = false;
     CK(timed(h, K_RES, [&] { return launch_residual(fa, h->stream); }));
     int rc = read_state(h, L);
@@ -760,7 +762,7 @@ template <typename T> struct FeSolve {
     if (!any) return RVE_OK;
     for (int l = 0; l < L; ++l) {
       h->cg_h[l].active = active[l];
-      h->cg_h[l].status = ST_RUN;
+      h->cg_h[l].status = hold ? ST_HOLD : ST_RUN;
       h->cg_h[l].it = 0;
       h->cg_h[l].maxit = max_iter - iters[l];
       // do not solve further than the outer tolerance needs: after a first
@@ -812,6 +814,7 @@ template <typename T> struct FeSolve {
       steps[l] += 1;
       cgrel[l] = h->cg_h[l].rr0 > 0 ? std::sqrt(h->cg_h[l].rr / h->cg_h[l].rr0) : 0.0;
       if (h->cg_h[l].status == ST_BAD) bad[l] = 1;
+      if (h->cg_h[l].pad == kTimeoutMark) timeout[l] = 1;
     }
     // u += (B^H B)^-1 B^H delta  (delta = CG iterate x; the nodal state added xi above)
     if (h->op_form != RVE_FORM_NODAL) {
@@ -837,7 +840,8 @@ template <typename T> struct FeSolve {
     int worst = RVE_OK;
     for (int l = 0; l < L; ++l) {
       int st = RVE_OK;
-      if (bad[l]) st = RVE_ERR_NONFINITE;
+      if (timeout[l]) st = RVE_ERR_TIMEOUT;
+      else if (bad[l]) st = RVE_ERR_NONFINITE;
       else if (frel[l] > rel_tol && !floor_hit[l]) st = RVE_ERR_NOT_CONVERGED;
       if (info) {
         info[l].iterations = iters[l];
@@ -847,7 +851,9 @@ template <typename T> struct FeSolve {
         info[l].rel_residual = frel[l];
         info[l].cg_rel_residual = cgrel[l];
       }
-      if (st == RVE_ERR_NONFINITE || (st != RVE_OK && worst == RVE_OK)) worst = st;
+      if (st == RVE_ERR_TIMEOUT || (st == RVE_ERR_NONFINITE && worst != RVE_ERR_TIMEOUT) ||
+          (st != RVE_OK && worst == RVE_OK))
+        worst = st;
     }
     return worst;
   }
@@ -873,6 +879,12 @@ int solve_impl(rve_s* h, const double* emac_host, int L, double rel_tol, int max
   return sv.finish(info);
 }
 
+// Release held slots of a handle: ST_HOLD -> ST_RUN (one block).
+__global__ void release_held(CgState* cg, int L) {
+  for (int l = threadIdx.x; l < L; l += blockDim.x)
+    if (cg[l].status == ST_HOLD) cg[l].status = ST_RUN;
+}
+
 // The projected-CG iterations of several handles (the size groups of a
 // batch) as ONE CUDA graph per batch of K iterations: a fork from the batch's
 // stream to every handle's stream, K iterations of every handle on its own
@@ -891,8 +903,11 @@ template <typename T> struct MultiRunner {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr, copied[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> join;
+  // pinned host copies of every handle's CG states, one per graph copy (the
+  // handles' own buffers stay free for their refinement steps)
+  std::vector<CgState*> hbuf[2];
 
-  CgState* host(int b, size_t i) { return b == 0 ? hs[i]->cg_h : hs[i]->cg_h2; }
+  CgState* host(int b, size_t i) { return hbuf[b][i]; }
 
   // Fork, K iterations of every handle, state copies, join (captured or direct).
   cudaError_t issue(int b) {
@@ -912,6 +927,14 @@ template <typename T> struct MultiRunner {
   MultiRunner(cudaStream_t root_, const std::vector<rve_s*>& hs_, const std::vector<int>& Ls_,
               const std::vector<PassArgs<T>>& as_, int K_)
       : root(root_), hs(hs_), Ls(Ls_), as(as_), K(K_), join(hs_.size(), nullptr) {
+    for (int b = 0; b < 2; ++b) {
+      hbuf[b].assign(hs.size(), nullptr);
+      for (size_t i = 0; i < hs.size(); ++i)
+        if (cudaMallocHost((void**)&hbuf[b][i], (size_t)Ls[i] * sizeof(CgState)) != cudaSuccess) {
+          cudaGetLastError();
+          hbuf[b][i] = nullptr;
+        }
+    }
     cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     for (auto& ev : join) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (int b = 0; b < 2; ++b) cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
@@ -944,6 +967,15 @@ template <typename T> struct MultiRunner {
     if (fork) cudaEventDestroy(fork);
     for (auto& ev : join)
       if (ev) cudaEventDestroy(ev);
+    for (int b = 0; b < 2; ++b)
+      for (auto* p : hbuf[b])
+        if (p) cudaFreeHost(p);
+  }
+  bool ok() const {
+    for (int b = 0; b < 2; ++b)
+      for (auto* p : hbuf[b])
+        if (!p) return false;
+    return true;
   }
   cudaError_t launch(int b) {
     cudaError_t e = exec[b] ? cudaGraphLaunch(exec[b], root) : issue(b);
@@ -974,47 +1006,67 @@ template <typename T> struct MultiRunner {
   }
   // Launch batches until every handle is done.  A handle whose inner solve has
   // finished (no active slot still iterating) is handed to transition(i) at
-  // once, with no graph in flight (the copies in flight are drained first);
-  // transition() queues that handle's next refinement step (or marks it done)
-  // and the launches resume, so every handle advances on its own while all of
-  // them share one graph.  max_batches bounds the launches.
+  // once, while the graph launched after that state copy is still in flight:
+  // the handle's slots are not running, so that graph's branch for it only
+  // exits early, and transition() prepares the next refinement step with the
+  // slots held (ST_HOLD).  The held slots are released by a kernel on the
+  // handle's stream that waits for the in-flight graph, and the next graph
+  // waits for the release, so a branch never sees a handle's state change in
+  // the middle of a graph.  A handle's state copies count again from the first
+  // graph launched after its release.  max_batches bounds the launches.
   template <class Transition>
   int drive(const std::vector<const std::vector<int>*>& active, std::vector<char>& done, Transition transition,
             long max_batches) {
-    std::vector<size_t> all(hs.size());
-    for (size_t i = 0; i < hs.size(); ++i) all[i] = i;
+    const size_t G = hs.size();
+    std::vector<size_t> all(G);
+    for (size_t i = 0; i < G; ++i) all[i] = i;
     if (int rc = sync_in(all)) return rc;
+    std::vector<long> valid_from(G, 0);   // first graph whose copy of the handle's state counts
+    long idx[2] = {-1, -1};               // graph last launched into each copy
+    long launched = 0;
     int cur = 0;
     if (cudaError_t e = launch(cur)) return map_err(e);
-    bool other = false;   // the other copy is in flight
-    for (long n = 1;; ++n) {
-      const bool ahead = n < max_batches;
-      if (ahead) {
+    idx[cur] = launched++;
+    bool other = false;                   // the other copy is in flight
+    for (;;) {
+      if (launched < max_batches) {
         if (cudaError_t e = launch(1 - cur)) return map_err(e);
+        idx[1 - cur] = launched++;
         other = true;
       }
       if (cudaError_t e = cudaEventSynchronize(copied[cur])) return map_err(e);
       std::vector<size_t> ready;
-      for (size_t i = 0; i < hs.size(); ++i)
-        if (!done[i] && idle(cur, i, *active[i])) ready.push_back(i);
-      if (ready.empty() && ahead) {
-        cur = 1 - cur;
+      for (size_t i = 0; i < G; ++i)
+        if (!done[i] && idx[cur] >= valid_from[i] && idle(cur, i, *active[i])) ready.push_back(i);
+      for (size_t i : ready) {
+        if (int rc = transition(i)) return rc;
+        if (done[i]) continue;
+        // release after the graph in flight (if any), before the next one
+        if (other && cudaStreamWaitEvent(hs[i]->stream, copied[1 - cur], 0) != cudaSuccess) {
+          cudaGetLastError();
+          return RVE_ERR_CUDA;
+        }
+        release_held<<<1, 64, 0, hs[i]->stream>>>(hs[i]->cg, Ls[i]);
+        if (cudaGetLastError() != cudaSuccess) return RVE_ERR_CUDA;
+        if (int rc = sync_in({i})) return rc;
+        valid_from[i] = launched;
+      }
+      bool all_done = true;
+      for (size_t i = 0; i < G; ++i) all_done = all_done && done[i];
+      if (all_done || !other) {
+        if (other) {
+          if (cudaError_t e = cudaEventSynchronize(copied[1 - cur])) return map_err(e);
+        }
+        if (int rc = sync_out()) return rc;
+        if (all_done || launched >= max_batches) return RVE_OK;
+        // nothing in flight and budget left (cannot happen with run-ahead on); restart
+        cur = 0;
+        if (cudaError_t e = launch(cur)) return map_err(e);
+        idx[cur] = launched++;
         continue;
       }
-      if (other) {
-        if (cudaError_t e = cudaEventSynchronize(copied[1 - cur])) return map_err(e);
-        other = false;
-      }
-      if (int rc = sync_out()) return rc;
-      if (!ahead) return RVE_OK;   // launch budget spent: the caller finishes every handle
-      for (size_t i : ready)
-        if (int rc = transition(i)) return rc;
-      bool all_done = true;
-      for (size_t i = 0; i < hs.size(); ++i) all_done = all_done && done[i];
-      if (all_done) return RVE_OK;
-      if (int rc = sync_in(ready)) return rc;
-      cur = 0;
-      if (cudaError_t e = launch(cur)) return map_err(e);
+      cur = 1 - cur;
+      other = false;
     }
   }
 };
@@ -1054,10 +1106,11 @@ int batch_lockstep(cudaStream_t root, const std::vector<rve_s*>& hs, const std::
       act[g] = &sv[g]->active;
     }
     MultiRunner<T> runner(root, hs, Ls, as, kCheckEvery);
+    if (!runner.ok()) return RVE_ERR_OOM;
     auto transition = [&](size_t g) -> int {
       if (int rc = sv[g]->after_inner()) return rc;
       bool need = false;
-      if (int rc = sv[g]->outer(&need)) return rc;
+      if (int rc = sv[g]->outer(&need, true)) return rc;
       if (!need) {
         done[g] = 1;
         return sv[g]->deactivate();

@@ -45,7 +45,13 @@ struct CgState {
   unsigned cnt_a, cnt_e, cnt_r, pad;
 };
 
-enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BAD = 3 };
+// ST_HOLD: set up for a new inner solve but not yet released to the CG
+// kernels (a batch handle whose next refinement step is being prepared while
+// the batch graph still runs the other handles).
+enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BAD = 3, ST_HOLD = 4 };
+// CgState::pad of a slot whose kernel gave up a bounded device-side wait
+// (status ST_BAD); the host reports RVE_ERR_TIMEOUT for it.
+constexpr unsigned kTimeoutMark = 0x7107u;
 
 // ------------------------------------------------------- FFT in shared memory
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
@@ -136,6 +142,15 @@ template <int N, int NT, bool B1_FAST = false, bool B2_FAST = false, int V = 0>
 __host__ __device__ constexpr bool warp_local_fft() {
   return FftSplit<N, V>::N1 == FftSplit<N, V>::N2 && !B1_FAST && !B2_FAST && 32 % FftSplit<N, V>::N1 == 0 &&
          NT % 32 == 0;
+}
+
+// Row stride of the x-transform buffers of the first and last passes: at
+// least the FFT's leading dimension, and 4 (mod 16) complex values, so that
+// the rows of the NP packed row pairs that consecutive threads read or write
+// at the same column (the two-for-one pre- and post-processing, row pairs
+// fastest) fall on different shared-memory banks.
+template <int N> __host__ __device__ constexpr int ae_ld() {
+  return FftSplit<N>::LD + ((4 - FftSplit<N>::LD % 16) + 16) % 16;
 }
 
 // Number of distinct splits of a length (1 or 2).
