@@ -80,3 +80,22 @@ def test_lognormal64_adjoint_sample_is_consistent():
     g = np.array(ref["adjoint_grad"])
     assert np.all(g > 0)                                            # J = C_1111 grows with every modulus
     assert len(set(ref["adjoint_voxels"])) == len(ref["adjoint_voxels"]) == 16
+
+
+def test_stored_256_mean_stress_is_admissible():
+    """The 256^3 log-normal field under a unit xx strain: the stored mean stress
+    is column 1 of an effective stiffness, so its xx entry lies between the
+    Reuss and Voigt values of that entry, the field is statistically isotropic
+    (yy and zz agree, shears are small), and the energy e_xx : C : e_xx is the
+    xx entry (positive)."""
+    ref = _load("lognormal256")
+    cfg = ms.config_inputs("lognormal256")
+    assert list(cfg["n"]) == ref["n"] and cfg["nu"] == ref["nu"]
+    S = np.array(ref["mean_stress"])
+    assert S.shape == (1, 6) and ref["iterations"][0] > 0
+    s = S[0]
+    V, R = voigt_reuss(cfg["E"], cfg["nu"], 3)
+    assert R[0, 0] <= s[0] <= V[0, 0]
+    assert abs(s[1] - s[2]) < 1e-3 * s[1]
+    assert np.abs(s[3:]).max() < 0.05 * s[0]
+    assert s[0] > s[1] > 0
