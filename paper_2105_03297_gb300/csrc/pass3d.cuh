@@ -589,8 +589,15 @@ cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   }
   return launch_a_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
 }
+// Tile variants of pass E: 0 default rows per block, 1 half, 2 double; 3
+// (FP32, n_x >= 128, CG iterations, with the spectrum's tensor map) the
+// pipelined persistent pass (pass3d_pipe.cuh); other modes of 3 use 0.
 template <typename T, int NX>
 cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && NX >= 128) {
+    if (a.var_e == 3 && a.emode == E_CG && a.tm_spec && a.L <= kPipeMaxL && a.n[1] >= kPipeETY)
+      return launch_e_3d_pipe<NX>(a, s);
+  }
   if constexpr (NX >= 64) {
     if (a.var_e == 1) return launch_e_3d_t<T, NX, tile_rows3<T>(1)>(a, s);
     if (a.var_e == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_e_3d_t<T, NX, tile_rows3<T>(2)>(a, s);

@@ -14,13 +14,14 @@
 // timeout mark, waits (bounded again) for its copies, and returns; the host
 // reports RVE_ERR_TIMEOUT.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the type only; the encoder comes from the driver entry point)
+
 #include <algorithm>
 
 #include "pass2d.cuh"
 
 namespace rve {
 
-constexpr int kPipeMaxL = 64;                  // load-case slots the per-slot partials hold
 constexpr long long kMbarWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -43,6 +44,10 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// Orders this thread's earlier shared-memory accesses before its later
+// async-proxy (TMA) accesses of the same memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned done;
   asm volatile(
@@ -60,10 +65,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
+// Dynamic shared memory is only guaranteed 16-byte alignment: the pipelined
+// passes round their base up to 128 bytes (TMA tensor copies need a 128-byte
+// aligned destination) and ask for kSmemAlignPad bytes more.
+constexpr int kSmemAlignPad = 128;
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) {
+  return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
+
 template <int NX, int TY> constexpr size_t pipe_a_smem() {
   // raw rows [3 streams][6 components][TY][NX] and the moduli [TY][NX] (FP32),
   // then the transform buffer [6][TY/2][ae_ld]
-  return sizeof(float) * (3 * 6 + 1) * TY * NX + sizeof(float2) * 6 * (TY / 2) * ae_ld<NX>();
+  return kSmemAlignPad + sizeof(float) * (3 * 6 + 1) * TY * NX + sizeof(float2) * 6 * (TY / 2) * ae_ld<NX>();
 }
 
 // grid: a multiple of the SM count (persistent), NT threads = the load units of
@@ -80,8 +93,9 @@ __global__ void __launch_bounds__(NT, 2) pass_a_3d_pipe(PassArgs<float> a) {
   constexpr int XV = NX / 4;                           // float4 vectors per row
   static_assert(NT == 2 * NP * XV, "one load unit per thread");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* stage = reinterpret_cast<T*>(smem_raw);           // [3][GS][ROW], then the moduli [ROW]
-  C* buf = reinterpret_cast<C*>(smem_raw + sizeof(T) * (3 * GS + 1) * ROW);
+  unsigned char* smem = align128(smem_raw);
+  T* stage = reinterpret_cast<T*>(smem);               // [3][GS][ROW], then the moduli [ROW]
+  C* buf = reinterpret_cast<C*>(smem + sizeof(T) * (3 * GS + 1) * ROW);
   __shared__ uint64_t bar;
   __shared__ double red[NT / 32];
   __shared__ double accl[kPipeMaxL];
@@ -209,7 +223,10 @@ __global__ void __launch_bounds__(NT, 2) pass_a_3d_pipe(PassArgs<float> a) {
     }
     __syncthreads();  // the stage is free and the transform buffer complete
     const int64_t tn = next_tile(t + gridDim.x);
-    if (tid == 0 && tn < total) issue(tn);
+    if (tid == 0 && tn < total) {
+      fence_proxy_async();
+      issue(tn);
+    }
     smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
     pass_a_store<T, NX, TY, NT, LD>(buf, GS, a.spec + ((((int64_t)l * a.m + grp * GS) * KX) * nz + z) * ny + y0,
                                     (int64_t)KX * nz * ny, (int64_t)nz * ny);
@@ -261,6 +278,229 @@ cudaError_t launch_a_3d_pipe(const PassArgs<float>& a, cudaStream_t s) {
   const int64_t tiles = (int64_t)(a.n[1] / TY) * a.n[2] * a.nq * a.L;
   const int blocks = (int)std::min<int64_t>(tiles, 2 * (int64_t)nsm);
   k<<<blocks, NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rve
+
+namespace rve {
+
+// ---------------------------------------------------------------- pass E
+// Pipelined last pass (3D, FP32, CG mode): the same arithmetic as pass_e_3d
+// in E_CG mode (inverse real FFT along x of the six components of a
+// tetrahedron group, r -= alpha q, <r, r>).  Each tile's spectrum (k_x = 0..n_x/2
+// of TY rows of one z plane: 6 x KX runs of TY complex values) arrives in one
+// TMA tensor copy (cp.async.bulk.tensor.4d over the spectrum's [comp][k_x][z][y]
+// layout), and its r rows in six bulk copies; the next tile's spectrum copy is
+// issued as soon as the current one is unpacked, its r rows as soon as the
+// current update has read them.  Bounded mbarrier waits as in the first pass.
+
+template <int NX, int TY> constexpr size_t pipe_e_smem() {
+  return kSmemAlignPad + sizeof(float2) * 6 * (NX / 2 + 1) * TY + sizeof(float) * 6 * TY * NX +
+         sizeof(float2) * 6 * (TY / 2) * ae_ld<NX>();
+}
+
+// One tensor copy of a 4D box at coordinates (c0 innermost .. c3) into shared memory.
+__device__ __forceinline__ void tensor_copy_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                               uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// r update of pass E from the staged rows: outputs x = k2 + N2 k1 of rows
+// (2 pr, 2 pr + 1) of component j; r rows read from shared memory, written to HBM.
+template <int NX, int TY>
+struct PipeEStore {
+  const float* rS;      // [6][TY][NX]
+  float* r;             // first component's r rows of the tile in HBM: r + j * N + row * NX + x
+  int64_t N;
+  float alpha;
+  float* acc;
+  __device__ __forceinline__ void batch(int b, int k2, const float2* q) const {
+    constexpr int NP = TY / 2;
+    constexpr int N1 = FftSplit<NX>::N1, N2 = FftSplit<NX>::N2;
+    const int j = b / NP, pr = b % NP;
+    const float* s0 = rS + (j * TY + 2 * pr) * NX + k2;
+    float* g0 = r + (int64_t)j * N + (int64_t)(2 * pr) * NX + k2;
+    float s = 0.f;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float a0 = s0[N2 * k1] - alpha * q[k1].x;
+      const float a1 = s0[NX + N2 * k1] - alpha * q[k1].y;
+      g0[N2 * k1] = a0;
+      g0[NX + N2 * k1] = a1;
+      s += a0 * a0 + a1 * a1;
+    }
+    *acc += s;
+  }
+  __device__ __forceinline__ void operator()(int, int, float2) const {}
+};
+
+template <int NX, int TY, int NT>
+__global__ void __launch_bounds__(NT, 2) pass_e_3d_pipe(PassArgs<float> a, const __grid_constant__ CUtensorMap tm) {
+  using T = float;
+  using C = float2;
+  constexpr int NP = TY / 2;
+  constexpr int GE = 6;
+  constexpr int KX = NX / 2 + 1;
+  constexpr int LD = ae_ld<NX>();
+  constexpr int ROW = TY * NX;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  C* specS = reinterpret_cast<C*>(smem);                                            // [GE][KX][TY]
+  T* rS = reinterpret_cast<T*>(smem + sizeof(C) * GE * KX * TY);                    // [GE][TY][NX]
+  C* buf = reinterpret_cast<C*>(smem + sizeof(C) * GE * KX * TY + sizeof(T) * GE * ROW);   // [GE][NP][LD]
+  __shared__ uint64_t barS, barR;
+  __shared__ double red[NT / 32];
+  __shared__ double accl[kPipeMaxL];
+  __shared__ int flag;
+
+  const int ny = a.n[1], nz = a.n[2], G = a.nq, L = a.L;
+  const int nyt = ny / TY;
+  const int64_t per_l = (int64_t)nyt * nz * G;
+  const int64_t total = per_l * L;
+  const int64_t N = a.N;
+  const int tid = threadIdx.x;
+
+  auto runs = [&](int l) -> bool {
+    const CgState* cg = a.cg + l;
+    return cg->active && (!a.cgphase || cg->status == ST_RUN);
+  };
+  auto next_tile = [&](int64_t t) -> int64_t {
+    for (; t < total; t += gridDim.x)
+      if (runs((int)(t / per_l))) return t;
+    return total;
+  };
+  auto decode = [&](int64_t t, int& l, int& grp, int& z, int& y0) {
+    l = (int)(t / per_l);
+    int64_t rem = t % per_l;
+    grp = (int)(rem / ((int64_t)nyt * nz));
+    rem %= (int64_t)nyt * nz;
+    z = (int)(rem / nyt);
+    y0 = (int)(rem % nyt) * TY;
+  };
+  auto issue_spec = [&](int64_t t) {
+    int l, grp, z, y0;
+    decode(t, l, grp, z, y0);
+    mbar_arrive_expect_tx(&barS, (unsigned)(sizeof(C) * GE * KX * TY));
+    // checked before the copy: a 128-byte aligned destination and a box inside
+    // the tensor (y0 a multiple of TY, the last component within the slots);
+    // otherwise the copy is skipped and the bounded wait reports the failure
+    const bool box_ok = (smem_u32(specS) & 127u) == 0 && (y0 % TY) == 0 && y0 + TY <= ny && z < nz &&
+                        l * a.m + grp * GE + GE <= a.L * a.m;
+    if (box_ok) tensor_copy_4d(specS, &tm, y0, z, 0, l * a.m + grp * GE, &barS);
+  };
+  auto issue_r = [&](int64_t t) {
+    int l, grp, z, y0;
+    decode(t, l, grp, z, y0);
+    const unsigned bytes = (unsigned)(ROW * sizeof(T));
+    const int64_t v0 = ((int64_t)z * ny + y0) * NX;
+    mbar_arrive_expect_tx(&barR, GE * bytes);
+    for (int j = 0; j < GE; ++j)
+      bulk_copy_g2s(rS + j * ROW, a.r + ((int64_t)l * a.m + grp * GE + j) * N + v0, bytes, &barR);
+  };
+
+  if (tid == 0) {
+    mbar_init(&barS, 1);
+    mbar_init(&barR, 1);
+    mbar_init_fence();
+  }
+  for (int l = tid; l < L; l += NT) accl[l] = 0.0;
+  __syncthreads();
+  int64_t t = next_tile(blockIdx.x);
+  if (tid == 0 && t < total) {
+    issue_spec(t);
+    issue_r(t);
+  }
+  unsigned parS = 0, parR = 0;
+  bool timed_out = false;
+  while (t < total) {
+    int l, grp, z, y0;
+    decode(t, l, grp, z, y0);
+    const T alpha = (T)a.cg[l].alpha;
+    const bool okS = mbar_wait_bounded(&barS, parS);
+    if (__syncthreads_or(!okS)) { timed_out = true; break; }
+    parS ^= 1u;
+    // two-for-one unpack of the staged spectrum into packed rows
+    for (int i = tid; i < GE * KX * NP; i += NT) {
+      const int pr = i % NP, k = (i / NP) % KX, j = i / (NP * KX);
+      const C* src = specS + (j * KX + k) * TY + 2 * pr;
+      C xa = src[0], xb = src[1];
+      if (k == 0 || k == NX / 2) { xa.y = 0; xb.y = 0; }  // C2R ignores these imaginary parts
+      C* row = buf + (j * NP + pr) * LD;
+      row[k] = mkc<T>(xa.x - xb.y, xa.y + xb.x);
+      if (k > 0 && k < NX / 2) row[NX - k] = mkc<T>(xa.x + xb.y, xb.x - xa.y);
+    }
+    __syncthreads();   // the spectrum stage is free, the rows are packed
+    const int64_t tn = next_tile(t + gridDim.x);
+    if (tid == 0 && tn < total) {
+      fence_proxy_async();
+      issue_spec(tn);
+    }
+    const bool okR = mbar_wait_bounded(&barR, parR);
+    if (__syncthreads_or(!okR)) { timed_out = true; break; }
+    parR ^= 1u;
+    T acc = 0;
+    const int64_t v0 = ((int64_t)z * ny + y0) * NX;
+    auto ld_s = [&](int b, int x) -> C { return buf[b * LD + x]; };
+    PipeEStore<NX, TY> st{rS, a.r + ((int64_t)l * a.m + grp * GE) * N + v0, N, alpha, &acc};
+    fft4<T, NX, GE * NP, LD, NT, +1, true, false, false, false, 0, decltype(ld_s), decltype(st), true>(buf, a.tw[0],
+                                                                                                     ld_s, st);
+    const double s = block_sum<NT>((double)acc, red);   // its barrier also ends the reads of the r stage
+    if (tid == 0) {
+      accl[l] += s;
+      if (tn < total) {
+        fence_proxy_async();
+        issue_r(tn);
+      }
+    }
+    t = tn;
+  }
+  if (timed_out) {
+    if (tid == 0) {
+      for (int l = 0; l < L; ++l) {
+        a.cg[l].status = ST_BAD;
+        a.cg[l].pad = kTimeoutMark;
+      }
+      __threadfence();
+    }
+    mbar_wait_bounded(&barS, parS);
+    mbar_wait_bounded(&barR, parR);
+    return;
+  }
+  __syncthreads();
+  for (int l = 0; l < L; ++l) {
+    if (!runs(l)) continue;
+    CgState* cg = a.cg + l;
+    double* part = a.part + (int64_t)l * a.part_stride;
+    if (publish_partial(accl[l], part, &cg->cnt_e, blockIdx.x, gridDim.x, &flag)) {
+      const double rr = sum_partials<NT>(part, gridDim.x, red);
+      if (tid == 0) finish_rr(cg, rr, false);
+    }
+    __syncthreads();
+  }
+}
+
+template <int NX>
+cudaError_t launch_e_3d_pipe(const PassArgs<float>& a, cudaStream_t s) {
+  constexpr int TY = kPipeETY;
+  constexpr int NT = 256;
+  constexpr size_t sm = pipe_e_smem<NX, TY>();
+  auto k = pass_e_3d_pipe<NX, TY, NT>;
+  static DeviceOnce attr;
+  static int sms[kMaxDevices] = {0};
+  const int dev = current_device();
+  attr.run(dev, [&] {
+    set_smem_attrs(k, sm);
+    if (dev >= 0 && dev < kMaxDevices) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  });
+  const int nsm = (dev >= 0 && dev < kMaxDevices && sms[dev] > 0) ? sms[dev] : 152;
+  const int64_t tiles = (int64_t)(a.n[1] / TY) * a.n[2] * a.nq * a.L;
+  const int blocks = (int)std::min<int64_t>(tiles, 2 * (int64_t)nsm);
+  k<<<blocks, NT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tm_spec));
   return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@
 //   RVE_FP64 runs the inner solve in FP64 (normally one outer step);
 //   RVE_MIXED runs it in FP32 and refines until the FP64 residual meets the
 //   tolerance.
+#include <cuda.h>   // CUtensorMap and its encoder's signature (looked up through the runtime)
+
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -30,6 +32,9 @@
 using namespace rve;
 
 struct rve_s {
+  // TMA tensor map of the first spectrum (3D, FP32), for the pipelined last pass
+  CUtensorMap tm_spec;
+  bool tm_ok = false;
   int dim = 0, n[3] = {1, 1, 1};
   int64_t N = 0;
   double len[3] = {1, 1, 1};
@@ -239,6 +244,45 @@ void free_L(rve_s* h) {
   h->Lcap = 0;
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime (no link
+// against the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of the first spectrum [slot][component][k_x][z][y] (complex FP32
+// copied as 8-byte elements), box = the pipelined last pass's tile: kPipeETY
+// values of y, one z, every k_x, the six components of a tetrahedron group.
+void make_spec_tensor_map(rve_s* h) {
+  h->tm_ok = false;
+  if (h->dim != 3 || h->tsize != 4 || h->n[0] < 128 || h->n[1] < kPipeETY || !h->spec) return;
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return;
+  const cuuint64_t ny = (cuuint64_t)h->n[1], nz = (cuuint64_t)h->n[2], kx = (cuuint64_t)h->kx;
+  const cuuint64_t dims[4] = {ny, nz, kx, (cuuint64_t)h->Lcap * h->m};
+  const cuuint64_t strides[3] = {ny * 8, nz * ny * 8, kx * nz * ny * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)kPipeETY, 1, (cuuint32_t)kx, 6};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(&h->tm_spec, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, h->spec, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  h->tm_ok = (r == CUDA_SUCCESS);
+}
+
 // Buffers for L load cases (grown, never shrunk).
 int ensure_capacity(rve_s* h, int L) {
   if (L <= h->Lcap) return RVE_OK;
@@ -294,6 +338,7 @@ int ensure_capacity(rve_s* h, int L) {
   if (keep_u) cudaFree(keep_u);
   CK(se);
   h->Lcap = L;
+  make_spec_tensor_map(h);
   CK(cudaGetLastError());
   return RVE_OK;
 }
@@ -328,6 +373,7 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   a.var_e = h->var[1] < 0 ? 0 : h->var[1];
   a.var_c = h->var[2] < 0 ? 0 : h->var[2];
   a.var_y = h->var[3] < 0 ? 0 : h->var[3];
+  a.tm_spec = h->tm_ok ? static_cast<const void*>(&h->tm_spec) : nullptr;
   return a;
 }
 
@@ -497,7 +543,7 @@ int split_count(int n) {
 int rve_sched_candidates(const rve_s* h, int which) {
   switch (which) {
     case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 6 : h->n[0] >= 64 ? 5 : 3;
-    case 1: return 3;
+    case 1: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128 && h->tm_ok) ? 4 : 3;
     case 2: return split_count(h->n[h->dim - 1]);
     default: return h->dim == 3 ? split_count(h->n[1]) : 1;
   }

@@ -52,6 +52,11 @@ enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BAD = 3, ST_HOLD = 4 };
 // CgState::pad of a slot whose kernel gave up a bounded device-side wait
 // (status ST_BAD); the host reports RVE_ERR_TIMEOUT for it.
 constexpr unsigned kTimeoutMark = 0x7107u;
+// The pipelined persistent passes (pass3d_pipe.cuh): load-case slots their
+// per-slot partial sums hold, and the rows per tile of the last pass (the
+// height of its spectrum tensor map's box).
+constexpr int kPipeMaxL = 64;
+constexpr int kPipeETY = 4;
 
 // ------------------------------------------------------- FFT in shared memory
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }

@@ -67,6 +67,7 @@ template <typename T> struct PassArgs {
   int var_a, var_e;  // tile variants of passes A (0..4) and E (0..2): see the launchers
   int var_c, var_y;  // FFT split variants (FftSplit<N, V>) of pass C's axis and of passes B / D (3D)
   int comp_in;       // number of components in the spectrum for this pass (m or D)
+  const void* tm_spec;  // host copy of the TMA tensor map of the first spectrum (3D FP32), or null
   int deriv;         // Deriv
 };
 
