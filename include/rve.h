@@ -366,6 +366,14 @@ int rve_batch_effective_tangent(rve_batch_t b, int index, double* C);
 int rve_apply_operator_2d_static(const int64_t* n, const double* length, const float* E, double nu,
                                  const float* p, float* q, int apply_material, void* cuda_stream);
 
+/* Test hook (the paper has no counterpart): with on != 0 the pipelined passes
+ * (schedule variant 5 of the first pass, 3 of the last) issue none of their
+ * copies, so that their bounded device-side waits run out; the solve then
+ * returns RVE_ERR_TIMEOUT after a few seconds and the handle stays usable once
+ * the hook is off again.  For testing the timeout path without a GPU fault;
+ * off by default, no effect on other schedules. */
+int rve_test_stall_copies(rve_t h, int on);
+
 /* Number of voxels N and strain scalars per voxel m of a handle. */
 int rve_sizes(rve_t h, int64_t* n_voxels, int* m, int* n_s, int* dim);
 

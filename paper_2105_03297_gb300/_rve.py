@@ -53,6 +53,7 @@ SIGNATURES = {
     "rve_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "rve_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "rve_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "rve_test_stall_copies": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_set_operator_form": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_set_derivative": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_set_kinematics": (C.c_int, [C.c_void_p, C.c_int]),
@@ -256,6 +257,10 @@ class RVE:
         """Force the schedule (-1 = autotune that entry at the next solve)."""
         v = (C.c_int * self.SCHED_PASSES)(int(var_a), int(var_e), int(var_c), int(var_y))
         _check(load().rve_set_schedule(self.h, v), "rve_set_schedule")
+
+    def test_stall_copies(self, on):
+        """Test hook: make the pipelined passes' bounded waits run out (see include/rve.h)."""
+        _check(load().rve_test_stall_copies(self.h, 1 if on else 0), "rve_test_stall_copies")
 
     FORMS = {"stress": 0, "factored": 1, "nodal": 2}
 

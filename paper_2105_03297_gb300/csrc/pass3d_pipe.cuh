@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(NT, 2) pass_a_3d_pipe(PassArgs<float> a) {
     const unsigned bytes = (unsigned)(ROW * sizeof(T));
     const int64_t v0 = ((int64_t)z * ny + y0) * NX;
     mbar_arrive_expect_tx(&bar, (unsigned)(streams * GS + 1) * bytes);
+    if (a.stall_copies) return;   // test hook: the phase never completes
     for (int s = 0; s < streams; ++s) {
       const T* base = s == 0 ? a.r : s == 1 ? a.p : a.x;
       for (int j = 0; j < GS; ++j)
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(NT, 2) pass_e_3d_pipe(PassArgs<float> a, const
     // otherwise the copy is skipped and the bounded wait reports the failure
     const bool box_ok = (smem_u32(specS) & 127u) == 0 && (y0 % TY) == 0 && y0 + TY <= ny && z < nz &&
                         l * a.m + grp * GE + GE <= a.L * a.m;
-    if (box_ok) tensor_copy_4d(specS, &tm, y0, z, 0, l * a.m + grp * GE, &barS);
+    if (box_ok && !a.stall_copies) tensor_copy_4d(specS, &tm, y0, z, 0, l * a.m + grp * GE, &barS);
   };
   auto issue_r = [&](int64_t t) {
     int l, grp, z, y0;
@@ -399,6 +400,7 @@ __global__ void __launch_bounds__(NT, 2) pass_e_3d_pipe(PassArgs<float> a, const
     const unsigned bytes = (unsigned)(ROW * sizeof(T));
     const int64_t v0 = ((int64_t)z * ny + y0) * NX;
     mbar_arrive_expect_tx(&barR, GE * bytes);
+    if (a.stall_copies) return;
     for (int j = 0; j < GE; ++j)
       bulk_copy_g2s(rS + j * ROW, a.r + ((int64_t)l * a.m + grp * GE + j) * N + v0, bytes, &barR);
   };

@@ -35,6 +35,7 @@ struct rve_s {
   // TMA tensor map of the first spectrum (3D, FP32), for the pipelined last pass
   CUtensorMap tm_spec;
   bool tm_ok = false;
+  int stall_copies = 0;  // test hook (rve_test_stall_copies)
   int dim = 0, n[3] = {1, 1, 1};
   int64_t N = 0;
   double len[3] = {1, 1, 1};
@@ -374,6 +375,7 @@ template <typename T> PassArgs<T> pass_args(const rve_s* h, int L, double* u, co
   a.var_c = h->var[2] < 0 ? 0 : h->var[2];
   a.var_y = h->var[3] < 0 ? 0 : h->var[3];
   a.tm_spec = h->tm_ok ? static_cast<const void*>(&h->tm_spec) : nullptr;
+  a.stall_copies = h->stall_copies;
   return a;
 }
 
@@ -1570,6 +1572,13 @@ int rve_destroy(rve_t h) {
   if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
+  return RVE_OK;
+}
+
+int rve_test_stall_copies(rve_t h, int on) {
+  DeviceScope dev_scope(h ? h->device : -1);
+  if (!h) return RVE_ERR_ARG;
+  h->stall_copies = on ? 1 : 0;
   return RVE_OK;
 }
 

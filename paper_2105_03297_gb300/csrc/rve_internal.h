@@ -68,6 +68,7 @@ template <typename T> struct PassArgs {
   int var_c, var_y;  // FFT split variants (FftSplit<N, V>) of pass C's axis and of passes B / D (3D)
   int comp_in;       // number of components in the spectrum for this pass (m or D)
   const void* tm_spec;  // host copy of the TMA tensor map of the first spectrum (3D FP32), or null
+  int stall_copies;     // test hook: the pipelined passes issue no copies, so their bounded waits run out
   int deriv;         // Deriv
 };
 

@@ -114,3 +114,26 @@ def test_pipelined_passes_run_the_same_cg(n):
     if n == (256, 16, 16):
         S_ref, _ = _oracle(n)
         assert rel_max(S[5, 3][0], S_ref) < 1e-9
+
+
+def test_pipelined_wait_that_runs_out_reports_a_timeout():
+    """Failure detection without a GPU fault: with the test hook on, the
+    pipelined passes issue none of their copies, so their bounded mbarrier waits
+    (about two seconds) run out; the solve must return RVE_ERR_TIMEOUT, and the
+    same handle must solve correctly once the hook is off (the context stays
+    usable)."""
+    from paper_2105_03297_gb300 import RVE, _rve
+    n = (256, 16, 16)
+    E = lognormal(n, 95)
+    with RVE(n, precision="mixed") as r:
+        r.set_schedule(5, 3, 0, 0)
+        r.set_material(E, 0.3)
+        r.test_stall_copies(True)
+        with pytest.raises(_rve.RveError) as err:
+            r.solve(EMAC[None], rel_tol=1e-12, max_iter=4000)
+        assert err.value.code == _rve.RVE_ERR_TIMEOUT
+        r.test_stall_copies(False)
+        code, info = r.solve(EMAC[None], rel_tol=1e-12, max_iter=4000)
+        assert code == 0, info
+        S_ref, _ = _oracle(n)
+        assert rel_max(r.mean_stress()[0], S_ref) < 1e-9
