@@ -137,17 +137,54 @@ template <int N, int V = 0> struct FftSplit {
   static constexpr int LDO = N + N2 + 1;
 };
 
-// True when the work items of every transform, in both steps of the
-// four-step FFT below, belong to one warp: a square split (N1 = N2, so both
-// steps give transform b the items b*N1 .. b*N1 + N1 - 1), items ordered
-// transform-major in both steps, N1 dividing the warp and NT a whole number
-// of warps.  The barriers between the steps then only have to order the
-// threads of one warp (__syncwarp orders their shared-memory accesses too).
-template <int N, int NT, bool B1_FAST = false, bool B2_FAST = false, int V = 0>
-__host__ __device__ constexpr bool warp_local_fft() {
-  return FftSplit<N, V>::N1 == FftSplit<N, V>::N2 && !B1_FAST && !B2_FAST && 32 % FftSplit<N, V>::N1 == 0 &&
-         NT % 32 == 0;
-}
+// Work items of the two steps of the four-step FFT below (step 1: (b, n1),
+// one per transform b and n1 < N1; step 2: (b, k2), k2 < N2).
+//   Warp mapping (WARP): when the split is square (N2 = N1) or N2 = 2 N1, the
+//   items are ordered transform-major in both steps and NT is a whole number
+//   of warps, warp w owns T = 32 / N2 whole transforms in both steps: step 1
+//   gives them to its first T N1 lanes (all lanes when square, half when
+//   N2 = 2 N1), step 2 to all of its lanes.  Every transform's data then stays
+//   inside one warp, and the barriers between the steps only have to order
+//   that warp's threads (__syncwarp orders their shared-memory accesses too).
+//   Otherwise items are numbered across the block (transform fastest where
+//   B*_FAST) and the steps need block-wide barriers.
+template <int N, int NB, int NT, bool B1_FAST = false, bool B2_FAST = false, int V = 0> struct FftItems {
+  static constexpr int N1 = FftSplit<N, V>::N1, N2 = FftSplit<N, V>::N2;
+  static constexpr bool WARP =
+      !B1_FAST && !B2_FAST && (N2 == N1 || N2 == 2 * N1) && NT % 32 == 0 && 32 % N2 == 0;
+  static constexpr int T = 32 / N2;                         // transforms per warp (warp mapping)
+  static constexpr int WB = (NT / 32) * T;                  // transforms per iteration (warp mapping)
+  static constexpr int W1 = NB * N1, W2 = NB * N2;
+  static constexpr int I1 = WARP ? (NB + WB - 1) / WB : (W1 + NT - 1) / NT;
+  static constexpr int I2 = WARP ? I1 : (W2 + NT - 1) / NT;
+  // item i of this thread in step 1 / step 2; false if the thread has none there
+  __device__ __forceinline__ static bool step1(int i, int& b, int& n1) {
+    if constexpr (WARP) {
+      const int lane = threadIdx.x & 31;
+      b = i * WB + (threadIdx.x >> 5) * T + lane / N1;
+      n1 = lane % N1;
+      return (T * N1 == 32 || lane < T * N1) && (NB % WB == 0 || b < NB);
+    } else {
+      const int it = threadIdx.x + i * NT;
+      b = B1_FAST ? it % NB : it / N1;
+      n1 = B1_FAST ? it / NB : it % N1;
+      return (W1 % NT) == 0 || it < W1;
+    }
+  }
+  __device__ __forceinline__ static bool step2(int i, int& b, int& k2) {
+    if constexpr (WARP) {
+      const int lane = threadIdx.x & 31;
+      b = i * WB + (threadIdx.x >> 5) * T + lane / N2;
+      k2 = lane % N2;
+      return NB % WB == 0 || b < NB;
+    } else {
+      const int it = threadIdx.x + i * NT;
+      b = B2_FAST ? it % NB : it / N2;
+      k2 = B2_FAST ? it / NB : it % N2;
+      return (W2 % NT) == 0 || it < W2;
+    }
+  }
+};
 
 // Row stride of the x-transform buffers of the first and last passes: at
 // least the FFT's leading dimension, and 4 (mod 16) complex values, so that
@@ -183,23 +220,21 @@ template <int N, int NB, int V = 0> constexpr int fft_threads() {
 //   step 2: for every (b, k2): FFT over n1 in registers, store X[k2 + N2 k1].
 // tw[t] = exp(-2 pi i t / N) (host FP64 libm, rounded to T).  The caller must
 // __syncthreads() before; the function ends with a barrier.  Every step reads
-// and writes only its own transform's row, so with a square split the
-// barriers inside are warp-level (warp_local_fft).
+// and writes only its own transform's row, so with the warp mapping of
+// FftItems the barriers inside are warp-level.
 template <typename T, int N, int NB, int LD, int NT, int S>
 __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
-  constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
-  constexpr bool LOCAL = warp_local_fft<N, NT>();
+  using It = FftItems<N, NB, NT>;
+  constexpr int N1 = It::N1, N2 = It::N2;
+  constexpr bool LOCAL = It::WARP;
   static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
-  constexpr int W1 = NB * N1, W2 = NB * N2;
-  constexpr int I1 = (W1 + NT - 1) / NT, I2 = (W2 + NT - 1) / NT;
   {
-    C v[I1][N2];
+    C v[It::I1][N2];
 #pragma unroll
-    for (int i = 0; i < I1; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W1 % NT) == 0 || it < W1) {
-        const int b = it / N1, n1 = it % N1;
+    for (int i = 0; i < It::I1; ++i) {
+      int b, n1;
+      if (It::step1(i, b, n1)) {
         const C* src = buf + b * LD + n1;
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) v[i][n2] = src[n2 * N1];
@@ -207,10 +242,9 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
     }
     fft_step_sync<LOCAL>();
 #pragma unroll
-    for (int i = 0; i < I1; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W1 % NT) == 0 || it < W1) {
-        const int b = it / N1, n1 = it % N1;
+    for (int i = 0; i < It::I1; ++i) {
+      int b, n1;
+      if (It::step1(i, b, n1)) {
         fft_reg<N2, S>(v[i]);
         C* dst = buf + b * LD + n1;
 #pragma unroll
@@ -228,12 +262,11 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
   }
   fft_step_sync<LOCAL>();
   {
-    C v[I2][N1];
+    C v[It::I2][N1];
 #pragma unroll
-    for (int i = 0; i < I2; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W2 % NT) == 0 || it < W2) {
-        const int b = it / N2, k2 = it % N2;
+    for (int i = 0; i < It::I2; ++i) {
+      int b, k2;
+      if (It::step2(i, b, k2)) {
         const C* src = buf + b * LD + k2 * (N1 + 1);
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) v[i][n1] = src[n1];
@@ -241,10 +274,9 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
     }
     fft_step_sync<LOCAL>();
 #pragma unroll
-    for (int i = 0; i < I2; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W2 % NT) == 0 || it < W2) {
-        const int b = it / N2, k2 = it % N2;
+    for (int i = 0; i < It::I2; ++i) {
+      int b, k2;
+      if (It::step2(i, b, k2)) {
         fft_reg<N1, S>(v[i]);
         C* dst = buf + b * LD + k2;
 #pragma unroll
@@ -267,36 +299,34 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
 //   BATCH_STORE: store.batch(b, k2, v) receives the N1 outputs of an item at
 //   once (k = k2 + N2 k1), so that it can issue all of its global loads first.
 // A load() or store() that touches buf touches only transform b's own row
-// (b*LD .. b*LD + LD - 1); so with a square split the barriers between the
-// steps are warp-level (warp_local_fft) and only the final STORE_SMEM barrier,
-// after which the caller reads across transforms, is block-wide.
+// (b*LD .. b*LD + LD - 1); so with the warp mapping of FftItems (square splits
+// and N2 = 2 N1) the barriers between the steps are warp-level, and only the
+// final STORE_SMEM barrier, after which the caller reads across transforms, is
+// block-wide.
 // V selects the split (FftSplit<N, V>).
 template <typename T, int N, int NB, int LD, int NT, int S, bool LOAD_SMEM, bool STORE_SMEM, bool B1_FAST,
           bool B2_FAST, int V = 0, class Load, class Store, bool BATCH_STORE = false>
 __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ tw, Load load, Store store) {
   using C = cplx<T>;
-  constexpr int N1 = FftSplit<N, V>::N1, N2 = FftSplit<N, V>::N2;
-  constexpr bool LOCAL = warp_local_fft<N, NT, B1_FAST, B2_FAST, V>();
+  using It = FftItems<N, NB, NT, B1_FAST, B2_FAST, V>;
+  constexpr int N1 = It::N1, N2 = It::N2;
+  constexpr bool LOCAL = It::WARP;
   static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
-  constexpr int W1 = NB * N1, W2 = NB * N2;
-  constexpr int I1 = (W1 + NT - 1) / NT, I2 = (W2 + NT - 1) / NT;
   {
-    C v[I1][N2];
+    C v[It::I1][N2];
 #pragma unroll
-    for (int i = 0; i < I1; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W1 % NT) == 0 || it < W1) {
-        const int b = B1_FAST ? it % NB : it / N1, n1 = B1_FAST ? it / NB : it % N1;
+    for (int i = 0; i < It::I1; ++i) {
+      int b, n1;
+      if (It::step1(i, b, n1)) {
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) v[i][n2] = load(b, n1 + N1 * n2);
       }
     }
     if (LOAD_SMEM) fft_step_sync<LOCAL>();
 #pragma unroll
-    for (int i = 0; i < I1; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W1 % NT) == 0 || it < W1) {
-        const int b = B1_FAST ? it % NB : it / N1, n1 = B1_FAST ? it / NB : it % N1;
+    for (int i = 0; i < It::I1; ++i) {
+      int b, n1;
+      if (It::step1(i, b, n1)) {
         fft_reg<N2, S>(v[i]);
         C* dst = buf + b * LD + n1;
 #pragma unroll
@@ -314,12 +344,11 @@ __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ t
   }
   fft_step_sync<LOCAL>();
   {
-    C v[I2][N1];
+    C v[It::I2][N1];
 #pragma unroll
-    for (int i = 0; i < I2; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W2 % NT) == 0 || it < W2) {
-        const int b = B2_FAST ? it % NB : it / N2, k2 = B2_FAST ? it / NB : it % N2;
+    for (int i = 0; i < It::I2; ++i) {
+      int b, k2;
+      if (It::step2(i, b, k2)) {
         const C* src = buf + b * LD + k2 * (N1 + 1);
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) v[i][n1] = src[n1];
@@ -327,10 +356,9 @@ __device__ __forceinline__ void fft4(cplx<T>* buf, const cplx<T>* __restrict__ t
     }
     if (STORE_SMEM) fft_step_sync<LOCAL>();
 #pragma unroll
-    for (int i = 0; i < I2; ++i) {
-      const int it = threadIdx.x + i * NT;
-      if ((W2 % NT) == 0 || it < W2) {
-        const int b = B2_FAST ? it % NB : it / N2, k2 = B2_FAST ? it / NB : it % N2;
+    for (int i = 0; i < It::I2; ++i) {
+      int b, k2;
+      if (It::step2(i, b, k2)) {
         fft_reg<N1, S>(v[i]);
         if constexpr (BATCH_STORE) {
           store.batch(b, k2, v[i]);  // outputs k = k2 + N2 k1, k1 < N1, in one call
