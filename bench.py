@@ -198,6 +198,17 @@ def model_bytes(dim, n, s, L_iters, form="stress"):
     return out
 
 
+def iteration_bytes(dim, n, s, form, mb):
+    """Bytes of one CG iteration of one load case and the model's description: the
+    scope table's model for the stress form, the sum of the form's per-kernel model
+    (model_bytes, per load-case iteration) for the factored and nodal forms."""
+    if form == "stress":
+        return scope_model_bytes(dim, n, s, s, s), ("(8 s_v + S s_f) m N + N s_E per load case: 8 vector and "
+                                                     "S = 4 (2D) / 8 (3D) spectrum streams; all passes of one CG "
+                                                     "iteration, CUDA-event times")
+    return float(sum(mb.values())), f"the {form} form's per-kernel byte model summed over one CG iteration"
+
+
 def scope_model_bytes(dim, n, s_v, s_f, s_E):
     """Bytes of one projected-CG iteration of one load case by the model of the
     hot-path scope table: (V s_v + S s_f) m N + N s_E with V = 8 vector streams
@@ -594,7 +605,7 @@ def other_workload(name, form, stream, reps=3):
     s = 4 if prec == "mixed" else 8
     mb = model_bytes(dim, n, s, lc_iters, form)
     cg_ms = sum(v[0] for k, v in kt.items() if k in mb) / (cg_iters * reps)
-    it_bytes = scope_model_bytes(dim, n, s, s, s) * lc_iters / cg_iters
+    it_bytes = iteration_bytes(dim, n, s, form, mb)[0] * lc_iters / cg_iters
     peak, _ = peaks()
     err = oracle_error(cfg_name, C=C if L == ns else None, S=C if L != ns else None)
     return {"grid": list(n), "load_cases": L, "precision": prec, "rel_tol": tol, "status": code,
@@ -624,6 +635,8 @@ def run_gpu(args):
     if args.workload.startswith("batch"):
         return run_batch(args, world, rank, local, dist)
     cfg_name, prec, tol = WORKLOADS[args.workload]
+    if args.rel_tol:
+        tol = args.rel_tol
     cfg = ms.config_inputs(cfg_name)
     n, E, nu, Em = cfg["n"], cfg["E"], cfg["nu"], cfg["E_macro"]
     dim = len(n)
@@ -680,9 +693,10 @@ def run_gpu(args):
     achieved = bytes_total / (dom_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     cg_ms = sum(v[0] for k, v in kt.items() if k in mb) / (cg_iters * args.steps)
-    # whole CG iteration on the scope table's model (V = 8 vector, S spectrum streams)
-    it_bytes = scope_model_bytes(dim, n, s_v=4 if prec == "mixed" else 8, s_f=4 if prec == "mixed" else 8,
-                                 s_E=4 if prec == "mixed" else 8) * lc_iters / cg_iters
+    # whole CG iteration: the scope table's model for the stress form (V = 8 vector,
+    # S spectrum streams), the form's own per-kernel model for the others
+    it_bytes, it_model = iteration_bytes(dim, n, s, args.form, mb)
+    it_bytes *= lc_iters / cg_iters
     it_achieved = it_bytes / (cg_ms * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers: E host->device, C_eff device->host
@@ -773,8 +787,7 @@ def run_gpu(args):
                      "peak_source": peak_kind},
         "roofline_iteration": {"bound": "hbm", "bytes_per_iteration": it_bytes, "achieved": it_achieved,
                                "peak": peak, "unit": "GB/s", "frac": it_achieved / peak, "peak_source": peak_kind,
-                               "model": "(8 s_v + S s_f) m N + N s_E per load case: 8 vector and S = 4 (2D) / 8 (3D) "
-                                        "spectrum streams; all passes of one CG iteration, CUDA-event times"},
+                               "model": it_model},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernels_hbm_frac": hbm_fractions(mb, kt, lc_iters, args.steps, peak),
         "schedule": dict(zip(("pass_a_tile_variant", "pass_e_tile_variant", "pass_c_fft_split", "pass_bd_fft_split"),
@@ -815,6 +828,8 @@ def main():
                          "e.g. 0,0 or 3,0,0,0 (default: autotune)")
     ap.add_argument("--form", default="stress", choices=["stress", "factored", "nodal"],
                     help="order of the operator inside CG (same operator; see include/rve.h)")
+    ap.add_argument("--rel-tol", type=float, default=0.0,
+                    help="override the workload's relative residual tolerance of the FP64 refinement")
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the FP64 GPU solve and cuFFT timings (context figures)")
     args = ap.parse_args()

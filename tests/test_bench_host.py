@@ -93,3 +93,13 @@ def test_extension_workloads_inputs():
             assert x["Em"].shape == (3 if len(x["n"]) == 2 else 6,) * 2
     assert (bench.extension_inputs("porous1024")["E"] == 0).mean() > 0.2
     assert not set(bench.EXTENSIONS) & set(bench.WORKLOADS)
+
+
+def test_iteration_bytes_per_form():
+    # the stress form uses the scope table's model; the other forms their own per-kernel model
+    n = (256, 256, 256)
+    b, note = bench.iteration_bytes(3, n, 4, "stress", {})
+    assert b == bench.scope_model_bytes(3, n, 4, 4, 4) and "8 vector" in note
+    mb = bench.model_bytes(3, n, 4, 1, "nodal")
+    b2, note2 = bench.iteration_bytes(3, n, 4, "nodal", mb)
+    assert b2 == sum(mb.values()) and "nodal" in note2 and b2 < 0.2 * b
