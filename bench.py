@@ -37,8 +37,12 @@ WORKLOADS = {
     "spheres128": ("spheres128", "mixed", 1e-11),
     "lognormal128": ("lognormal128", "mixed", 1e-10),
     "batch64": ("batch64", "mixed", 1e-10),
-    "lognormal256": ("lognormal256", "mixed", 1e-10),
-    "lognormal256_fp64": ("lognormal256", "fp64", 1e-10),
+    # the 256^3 headline stops at a residual reduction of 1e-9, which meets the
+    # 1e-9 bar under either reading: as the CG residual criterion, and as the
+    # mean-stress error against the oracle (measured 8.7e-13; 1e-10 gives 4e-14,
+    # 1e-8 gives 1.2e-11); the error is printed with every line
+    "lognormal256": ("lognormal256", "mixed", 1e-9),
+    "lognormal256_fp64": ("lognormal256", "fp64", 1e-9),
     # profiling sizes: the 256-point transforms of the 256^3 workload on a few GB
     "lognormal256x256x32": ("lognormal256x256x32", "mixed", 1e-10),
     "lognormal32x32x256": ("lognormal32x32x256", "mixed", 1e-10),
@@ -376,6 +380,26 @@ def golden_iterations(cfg_name):
     return its, d.get("C_eff")
 
 
+def oracle_iterations_at(cfg_name, tol):
+    """CG iterations the oracle needs, per load case, to bring its relative
+    residual to tol, read from the stored residual histories; without a history
+    (or for a tol below the stored solve's), the stored solve's own counts.
+    Returns (iterations, the tolerance they belong to)."""
+    d = golden(cfg_name)
+    hists = d.get("rel_residual_history")
+    if hists and tol >= d.get("tol", 0.0):
+        its = []
+        for h in hists:
+            k = next((i for i, v in enumerate(h) if v <= tol), None)
+            if k is None:
+                break
+            its.append(k)
+        else:
+            return its, tol
+    its, _ = golden_iterations(cfg_name)
+    return its, (d.get("tol") if its else None)
+
+
 def oracle_error(cfg_name, C=None, S=None):
     """Relative difference (max norm over max entry) of a GPU result from the
     stored oracle result: the effective tangent C when the golden file has one and
@@ -396,9 +420,11 @@ def run_reference(args):
     if rank != 0:
         return
     cfg_name, prec, tol = WORKLOADS[args.workload]
+    if args.rel_tol:
+        tol = args.rel_tol
     import microstructures as ms
     cfg = ms.config_inputs(cfg_name)
-    its_gold, _ = golden_iterations(cfg_name)
+    its_gold, its_tol = oracle_iterations_at(cfg_name, tol)
     total_its = sum(its_gold) if its_gold else None
     # one step = one oracle CG iteration (on the sample grid, see ORACLE_SAMPLE_GRID)
     o = OracleCG(cfg_name)
@@ -414,7 +440,7 @@ def run_reference(args):
     solve_s = sec_it * total_its if total_its else None
     value = (1.0 / solve_s) if solve_s else None
     sample = o.describe(cfg_name, args.steps) + (f"; a solve = the {total_its} CG iterations the oracle needs "
-                                                  f"for the stored result" if total_its else "")
+                                                  f"to a relative residual of {its_tol:g}" if total_its else "")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_step * 1e3,
@@ -800,13 +826,14 @@ def run_gpu(args):
     }
     out.update(extras)
     if rank == 0 and not args.no_cpu_baseline:
-        its_gold, _ = golden_iterations(cfg_name)
+        its_gold, its_tol = oracle_iterations_at(cfg_name, tol)
         total_its = sum(its_gold) if its_gold else lc_iters
         sec_it, its, cores, desc = oracle_sample(cfg_name, seconds_budget=15.0)
         v = 1.0 / (sec_it * total_its)
+        what = (f"the {total_its} iterations the oracle needs to a relative residual of {its_tol:g}"
+                if its_gold else f"the GPU solve's {total_its:g} iterations")
         out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                               "sample": f"{desc} ({sec_it * 1e3:.0f} ms per iteration), times the {total_its} "
-                                         f"iterations of the oracle's solve",
+                               "sample": f"{desc} ({sec_it * 1e3:.0f} ms per iteration), times {what}",
                                "host": host_cpu()}
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -598,14 +598,17 @@ class Problem:
             rr = rr_new
             yield x, rr, rr0
 
-    def solve(self, Emac, tol=1e-12, maxit=10000):
+    def solve(self, Emac, tol=1e-12, maxit=10000, history=None):
         """Solve G C (E + eps~) = 0 (Eq. stat-mech-equi2) for the compatible fluctuation
         eps~ by the projected CG (see cg); stop when ||r|| <= tol ||r_0|| (at once
         when r_0 = 0, a homogeneous cell).  Returns (eps_total, iterations,
-        relative residual)."""
+        relative residual).  A list passed as history receives ||r_k|| / ||r_0||
+        for k = 0, 1, ... (bookkeeping only)."""
         it = -1
         for x, rr, rr0 in self.cg(Emac):
             it += 1
+            if history is not None:
+                history.append(0.0 if rr0 == 0.0 else float(np.sqrt(rr / rr0)))
             if rr0 == 0.0 or it >= maxit or rr <= tol * tol * rr0:
                 break
         rel = 0.0 if rr0 == 0.0 else np.sqrt(rr / rr0)

@@ -9,7 +9,8 @@ iteration counts.  ``disc32`` is also solved by the assembled FEM (O2) and
 both results are stored.  ``lognormal64`` additionally stores the oracle's
 adjoint gradient of J = C_1111 at 16 seeded voxels and its Euler sum.
 ``batch4`` stores the tangents of the first RVE of each side (64, 128, 256,
-512) of the 64-RVE uneven batch.
+512) of the 64-RVE uneven batch.  Workloads with fewer load cases than
+strain components store the mean stresses and each solve's residual history.
 ``spheres128`` is solved one load case per process (``spheres128:<l>``, each
 writes ``spheres128_lc<l>.json``); ``spheres128:merge`` assembles
 ``spheres128.json`` from the six parts.  Nothing here calls the CUDA path.
@@ -105,12 +106,18 @@ def _run(name):
         else:
             S = []
             its = []
+            hists = []
             for row in Em:
-                eps, it, _ = P.solve(row, tol=TOL)
+                hist = []
+                eps, it, _ = P.solve(row, tol=TOL, history=hist)
                 S.append(P.mean_stress(eps).tolist())
                 its.append(it)
+                hists.append(hist)
             out["mean_stress"] = S
             out["iterations"] = its
+            # ||r_k|| / ||r_0|| for k = 0..iterations: how many iterations the
+            # oracle needs for a looser tolerance
+            out["rel_residual_history"] = hists
         if name == "disc32":
             from oracle.fem_assembly import AssembledFEM
             C2, _ = AssembledFEM(cfg["n"], cfg["E"], cfg["nu"]).effective_tangent(I)

@@ -60,6 +60,22 @@ def test_oracle_error_uses_the_stored_result():
     assert bench.oracle_error("no_such_workload", C=C) is None
 
 
+def test_oracle_iterations_at_reads_the_residual_history(monkeypatch):
+    stored = {"tol": 1e-12, "iterations": [6, 5],
+              "rel_residual_history": [[1.0, 0.3, 2e-8, 5e-10, 1e-11, 1e-12, 9e-13],
+                                       [1.0, 1e-9, 1e-10, 1e-11, 1e-12, 5e-13]]}
+    monkeypatch.setattr(bench, "golden", lambda name: stored)
+    assert bench.oracle_iterations_at("x", 1e-9) == ([3, 1], 1e-9)
+    assert bench.oracle_iterations_at("x", 1e-8) == ([3, 1], 1e-8)
+    assert bench.oracle_iterations_at("x", 1e-12) == ([5, 4], 1e-12)
+    # tighter than the stored solve: its own counts, at its own tolerance
+    assert bench.oracle_iterations_at("x", 1e-13) == ([6, 5], 1e-12)
+    del stored["rel_residual_history"]
+    assert bench.oracle_iterations_at("x", 1e-9) == ([6, 5], 1e-12)
+    monkeypatch.setattr(bench, "golden", lambda name: {})
+    assert bench.oracle_iterations_at("x", 1e-9) == (None, None)
+
+
 def test_host_cpu_description():
     h = bench.host_cpu()
     assert isinstance(h["model"], str) and h["model"] and h["nproc"] >= 1

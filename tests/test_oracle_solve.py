@@ -123,3 +123,25 @@ def test_disc32_matches_fem():
     C1, _, _ = P.effective_tangent(np.eye(3), tol=1e-13)
     C2, _ = AssembledFEM(cfg["n"], cfg["E"], cfg["nu"]).effective_tangent(np.eye(3))
     assert np.abs(C1 - C2).max() <= 1e-12 * np.abs(C2).max()
+
+
+def test_residual_history_records_each_iteration():
+    """The history a solve records is ||r_k|| / ||r_0||: it starts at 1, has one
+    entry per iteration, ends at the returned residual, and only its last entry
+    is at or below the tolerance.  A residual history recomputed from the
+    iterate (r_k = -A(E + eps~_k)) after k steps agrees with it."""
+    n = (8, 6)
+    E = _lognormal(n, 7)
+    P = Problem(n, E, 0.3)
+    Em = np.array([1.0, 0.0, 0.0])
+    hist = []
+    eps, it, res = P.solve(Em, tol=1e-10, history=hist)
+    assert len(hist) == it + 1 and hist[0] == 1.0 and hist[-1] == res
+    assert hist[-1] <= 1e-10 and min(hist[:-1]) > 1e-10
+    k = it // 2
+    h2 = []
+    eps_k, _, _ = P.solve(Em, tol=0.0, maxit=k, history=h2)
+    assert h2 == hist[:k + 1]
+    r0 = P.operator(P.broadcast_macro(Em))
+    rk = P.operator(eps_k)
+    assert abs(np.linalg.norm(rk) / np.linalg.norm(r0) - hist[k]) < 1e-8
