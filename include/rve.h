@@ -176,10 +176,16 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  *      thread per 16-byte load unit of the tile; in 3D with RVE_MIXED and
  *      n_x >= 128 also 5, a persistent pipelined pass whose next tile's rows
  *      arrive by bulk copies while the current tile is transformed (CG
- *      iterations of up to 64 load cases; otherwise it runs as 0).  A bounded
- *      device-side wait of that pass that gives up makes the solve return
+ *      iterations of up to 64 load cases; otherwise it runs as 0), and 6,
+ *      variant 0 whose blocks each ask for a later block's rows to be
+ *      prefetched into L2 (a hint: no wait, same arithmetic).  A bounded
+ *      device-side wait of variant 5 that gives up makes the solve return
  *      RVE_ERR_TIMEOUT;
  *  [1] the last pass (inverse x FFT + CG update): 0 default rows, 1 half, 2 double;
+ *      in 3D with RVE_MIXED and n_x >= 128 also 3, a persistent pipelined
+ *      pass whose next spectrum tile arrives by one tensor copy (same
+ *      conditions and timeout as variant 5 of the first pass), and 4, variant
+ *      0 with the L2 prefetch of a later block's spectrum tile and rows;
  *  [2] the split N = N1 * N2 of the four-step FFT along the last axis (y in
  *      2D, z in 3D; the pass that applies the projection): 0 the most square
  *      split, 1 half N1 and twice N2 (16 = 2 x 8, 32 = 2 x 16, 64 = 4 x 16,
@@ -191,7 +197,7 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  * rve_schedule also returns the measured candidate times
  * candidate_ms[RVE_SCHED_PASSES][RVE_SCHED_VARIANTS] (0 where a candidate does
  * not exist or was not timed; may be NULL). */
-enum { RVE_SCHED_PASSES = 4, RVE_SCHED_VARIANTS = 6 };
+enum { RVE_SCHED_PASSES = 4, RVE_SCHED_VARIANTS = 7 };
 int rve_schedule(rve_t h, int* variants, float* candidate_ms);
 int rve_set_schedule(rve_t h, const int* variants);
 

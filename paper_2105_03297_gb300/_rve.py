@@ -242,11 +242,11 @@ class RVE:
         _check(load().rve_get_strain(self.h, int(load_case), p, flag), "rve_get_strain")
         return out
 
-    SCHED_PASSES, SCHED_VARIANTS = 4, 6
+    SCHED_PASSES, SCHED_VARIANTS = 4, 7
 
     def schedule(self):
         """(variants [pass A, pass E, split of pass C's axis, split of the y axis],
-        candidate times [4][6] in ms)."""
+        candidate times [4][7] in ms)."""
         v = (C.c_int * self.SCHED_PASSES)()
         t = (C.c_float * (self.SCHED_PASSES * self.SCHED_VARIANTS))()
         _check(load().rve_schedule(self.h, v, t), "rve_schedule")

@@ -27,6 +27,86 @@ __host__ __device__ constexpr int kuhn_perm(int t, int i) {
                   : (i == 0 ? 2 : i == 1 ? 1 : 0);
 }
 
+// --------------------------------------------- L2 prefetch of a later tile
+// Passes A and E run grids of (n_y/TY, n_z, L*G) blocks, far more than are
+// resident, and the blocks start in about linear launch order as earlier ones
+// retire.  With a.pf_ahead = D > 0 every block asks the TMA unit to bring the
+// rows of block b + D (b its own linear index) into L2 (bulk prefetches: no
+// data reaches the SM and nothing waits on them), so that DRAM keeps streaming
+// a later tile while this block transforms its own.  Decomposes a linear
+// block index of that grid; false past the end of the grid or for a load case
+// whose CG has stopped.
+// Block coordinates (x, y, z) of the block a.pf_ahead places after this one in
+// launch order; false past the end of the grid.
+template <typename T>
+__device__ __forceinline__ bool grid_ahead(const PassArgs<T>& a, int& bx, int& by, int& bz) {
+  const int64_t nblk = (int64_t)gridDim.x * gridDim.y * gridDim.z;
+  const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z) + a.pf_ahead;
+  if (b >= nblk) return false;
+  bx = (int)(b % gridDim.x);
+  const int64_t b1 = b / gridDim.x;
+  by = (int)(b1 % gridDim.y);
+  bz = (int)(b1 / gridDim.y);
+  return true;
+}
+// Whether load case l still runs (its rows are worth prefetching).
+template <typename T> __device__ __forceinline__ bool slot_runs(const PassArgs<T>& a, int l) {
+  const CgState* cg = a.cg + l;
+  return cg->active && !(a.cgphase && cg->status != ST_RUN);
+}
+// Passes A and E: tile (l, grp, z, y0) of the later block.
+template <typename T>
+__device__ __forceinline__ bool block_ahead(const PassArgs<T>& a, int G, int TY, int& l, int& grp, int& z, int& y0) {
+  int bx, bz;
+  if (!grid_ahead(a, bx, z, bz)) return false;
+  y0 = bx * TY;
+  l = bz / G;
+  grp = bz % G;
+  return slot_runs(a, l);
+}
+
+// Pass A (CG mode, stress form): the r, E and (after the first iteration)
+// p_old and x rows of the later block: TY contiguous rows of NX values per
+// component, 19 requests of TY * NX * sizeof(T) bytes, one per thread.
+template <typename T, int NX, int TY>
+__device__ __forceinline__ void pass_a_prefetch_ahead(const PassArgs<T>& a, int G) {
+  static_assert((TY * NX * sizeof(T)) % 16 == 0, "bulk prefetch sizes are multiples of 16 bytes");
+  const int t = threadIdx.x;
+  if (t >= 19) return;
+  int l, grp, z, y0;
+  if (!block_ahead(a, G, TY, l, grp, z, y0)) return;
+  if (t >= 7 && a.cg[l].it == 0) return;   // no p_old or x reads in the first iteration
+  const int64_t N = a.N;
+  const int64_t row0 = ((int64_t)z * a.n[1] + y0) * NX;
+  const int64_t comp = ((int64_t)l * a.m + grp * 6) * N + row0;
+  const T* src = t < 6 ? a.r + comp + t * N
+               : t == 6 ? a.E + (int64_t)(l / a.lcs) * N + row0
+               : t < 13 ? a.p + comp + (t - 7) * N
+                        : a.x + comp + (t - 13) * N;
+  prefetch_l2_bulk(src, (unsigned)(TY * NX * sizeof(T)));
+}
+
+// Pass E (CG mode, stress form): the later block's spectrum tile (TY
+// contiguous y values for each of its six components and NX/2 + 1 k_x) and its
+// r rows.
+template <typename T, int NX, int TY>
+__device__ __forceinline__ void pass_e_prefetch_ahead(const PassArgs<T>& a, int G) {
+  constexpr int KX = NX / 2 + 1;
+  static_assert((TY * sizeof(cplx<T>)) % 16 == 0, "bulk prefetch sizes are multiples of 16 bytes");
+  static_assert((TY * NX * sizeof(T)) % 16 == 0, "bulk prefetch sizes are multiples of 16 bytes");
+  int l, grp, z, y0;
+  if (!block_ahead(a, G, TY, l, grp, z, y0)) return;
+  const int ny = a.n[1], nz = a.n[2];
+  const cplx<T>* s0 = a.spec + ((((int64_t)l * a.m + grp * 6) * KX) * nz + z) * ny + y0;
+  const T* r0 = a.r + ((int64_t)l * a.m + grp * 6) * a.N + ((int64_t)z * ny + y0) * NX;
+  for (int i = threadIdx.x; i < 6 * KX + 6; i += blockDim.x) {
+    if (i < 6 * KX)
+      prefetch_l2_bulk(s0 + (int64_t)i * nz * ny, (unsigned)(TY * sizeof(cplx<T>)));   // i = c KX + k_x
+    else
+      prefetch_l2_bulk(r0 + (int64_t)(i - 6 * KX) * a.N, (unsigned)(TY * NX * sizeof(T)));
+  }
+}
+
 // ---------------------------------------------------------------- pass A
 // Resident blocks per SM the register budget is sized for.
 template <typename T, int NT> __host__ __device__ constexpr int pass_a_min_blocks() {
@@ -59,6 +139,7 @@ __global__ void __launch_bounds__(NT, pass_a_min_blocks<T, NT>()) pass_a_3d(Pass
   T beta = 0, alpha_prev = 0;
   bool use_old = false;
   if (a.amode == A_CG) { beta = (T)cg->beta; alpha_prev = (T)cg->alpha; use_old = cg->it > 0; }
+  if (a.pf_ahead > 0 && a.amode == A_CG && !nodal) pass_a_prefetch_ahead<T, NX, TY>(a, G);
   // two columns per unit: 6 components x 2 rows x (r, p, x) stay in registers
   const T acc = pass_a_load<T, NX, TY, GS, NT, LD, 2>(a, buf, l, c0, ((int64_t)z * ny + y0) * NX, nodal, beta,
                                                       alpha_prev, use_old);
@@ -98,6 +179,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT <= 256 ? 4 : 2) : 1) 
   const int64_t cbase = (((int64_t)l * a.m + c) * KX + kx);
   C* pencils = a.spec + (cbase * nz + z0) * NY;  // [zz][y], y contiguous
   C* chunks = a.spec2 + cbase * NY * nz + z0;     // [k_y][zz], zz contiguous
+  // L2 prefetch of the later block's input (see grid_ahead): forward, its
+  // TZB contiguous y-pencils (one request); inverse, its NY z-chunks of TZB
+  // values
+  int zb2, kx2, lc2;
+  if (a.pf_ahead > 0 && grid_ahead(a, zb2, kx2, lc2) && slot_runs(a, lc2 / Cc)) {
+    static_assert((TZB * sizeof(C)) % 16 == 0, "bulk prefetch sizes are multiples of 16 bytes");
+    const int64_t cb2 = (((int64_t)(lc2 / Cc) * a.m + lc2 % Cc) * KX + kx2);
+    const int z2 = zb2 * TZB;
+    if (FWD) {
+      if (threadIdx.x == 0) prefetch_l2_bulk(a.spec + (cb2 * nz + z2) * NY, (unsigned)(TZB * NY * sizeof(C)));
+    } else {
+      for (int k = threadIdx.x; k < NY; k += blockDim.x)
+        prefetch_l2_bulk(a.spec2 + cb2 * NY * nz + z2 + (int64_t)k * nz, (unsigned)(TZB * sizeof(C)));
+    }
+  }
   if (FWD) {
     // step 1 reads whole y-pencils, step 2 writes z-chunks (zz fastest)
     auto ld = [&](int zz, int y) -> C { return pencils[(int64_t)zz * NY + y]; };
@@ -337,6 +433,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 576) ? 2 : 1) pas
   const int cout = (a.pmode == P_NODAL_OUT || a.pmode == P_SOLVE) ? 3 : M;
   const int64_t stride_c = (int64_t)KX * ny * NZ;
   C* pen = a.spec2 + (int64_t)l * M * stride_c + ((int64_t)kx * ny + ky) * NZ;
+  // L2 prefetch of the later block's pencil (see grid_ahead): one request of
+  // NZ values per component
+  int kx2, ky2, l2;
+  if (a.pf_ahead > 0 && threadIdx.x < M && grid_ahead(a, kx2, ky2, l2) && slot_runs(a, l2))
+    prefetch_l2_bulk(a.spec2 + (int64_t)l2 * M * stride_c + ((int64_t)kx2 * ny + ky2) * NZ + threadIdx.x * stride_c,
+                     (unsigned)(NZ * sizeof(C)));
   auto ld_g = [&](int c, int z) -> C { return pen[c * stride_c + z]; };
   auto st_s = [&](int c, int k, C v) { buf[c * LD + k] = v; };
   if (cin == M) fft4<T, NZ, M, LD, NT, -1, false, true, false, false, V>(buf, a.tw[2], ld_g, st_s);
@@ -510,6 +612,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 384) ? 3 : 1) pas
   // 4 KB rows compete with the spectrum loads at the start of the block)
   if (a.emode == E_CG)
     prefetch_rows_l2<T, NX>(a.r + ((int64_t)l * a.m + c0) * N + ((int64_t)z * ny + y0) * NX, ge, TY, N);
+  if (a.pf_ahead > 0 && a.emode == E_CG && !nodal) pass_e_prefetch_ahead<T, NX, TY>(a, G);
 
   pass_e_unpack<T, NX, TY, NT, LD>(buf, a.spec + ((((int64_t)l * a.m + c0) * KX) * nz + z) * ny + y0, ge,
                                    (int64_t)KX * nz * ny, (int64_t)nz * ny);
@@ -548,34 +651,74 @@ template <typename T> constexpr int tile_rows3(int v) {
 template <typename T, int NX, int TY> constexpr int pass_a_units3() { return 2 * (TY / 2) * (NX / Vec16<T>::n); }
 template <int A, int B> constexpr int max_i() { return A > B ? A : B; }
 
+// Prefetch distance (blocks ahead, see grid_ahead): the blocks resident at once
+// (occ per SM x SMs) divided by div.  What pays is about 4 to 10 MB of
+// prefetched rows in flight, so the divisor depends on a block's input.
+// Measured at 256^3 (FP32, ms per CG iteration):
+//   pass A (152 KB per block, three blocks per SM), div 16 (28 blocks): 2.88
+//     without, 2.53 at div 16, 2.56 at div 32 to 152, 2.62 at div 8 and 3.26
+//     at div 2 (35 MB in flight crowd L2);
+//   pass B (32 KB per block): 0.86 without, 0.81 / 0.77 / 0.72 / 0.69 / 0.72
+//     at div 16 / 8 / 4 / 2 / 1;
+//   pass C (72 KB per block): 1.52 without, 1.55 / 1.53 / 1.47 / 1.41 / 1.43;
+//   pass D (32 KB per block, scattered z-chunks): 0.85 without, 0.83 / 0.82 /
+//     0.82 / 0.82 / 0.84.
+inline int prefetch_distance(int occ, int div) {
+  const int d = occ * device_sm_count() / div;
+  return d > 1 ? d : 1;
+}
+
 template <typename T, int NX, int TY, bool BY_UNITS = false>
-cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t launch_a_3d_t(const PassArgs<T>& a, cudaStream_t s, bool ahead = false) {
   constexpr int NF = fft_threads<NX, 6 * (TY / 2)>();
   constexpr int NU = (pass_a_units3<T, NX, TY>() + 31) / 32 * 32;
   constexpr int NT = BY_UNITS ? (max_i<NF, NU>() > 1024 ? NF : max_i<NF, NU>()) : NF;
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * ae_ld<NX>();
   auto k = pass_a_3d<T, NX, TY, NT>;
   static DeviceOnce attr;
-  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
+  static int occ[kMaxDevices] = {0};
+  const int dev = current_device();
+  attr.run(dev, [&] {
+    set_smem_attrs(k, sm);
+    if (dev >= 0 && dev < kMaxDevices) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[dev], k, NT, sm);
+  });
   dim3 grid(a.n[1] / TY, a.n[2], a.L * (a.amode == A_NODAL ? 1 : a.nq));
-  k<<<grid, NT, sm, s>>>(a);
+  if (ahead) {
+    PassArgs<T> b = a;
+    b.pf_ahead = prefetch_distance((dev >= 0 && dev < kMaxDevices) ? occ[dev] : 0, 16);
+    k<<<grid, NT, sm, s>>>(b);
+  } else {
+    k<<<grid, NT, sm, s>>>(a);
+  }
   return cudaGetLastError();
 }
 template <typename T, int NX, int TY>
-cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t launch_e_3d_t(const PassArgs<T>& a, cudaStream_t s, bool ahead = false) {
   constexpr int NT = fft_threads<NX, 6 * (TY / 2)>();
   const size_t sm = sizeof(cplx<T>) * 6 * (TY / 2) * ae_ld<NX>();
   auto k = pass_e_3d<T, NX, TY, NT>;
   static DeviceOnce attr;
-  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
+  static int occ[kMaxDevices] = {0};
+  const int dev = current_device();
+  attr.run(dev, [&] {
+    set_smem_attrs(k, sm);
+    if (dev >= 0 && dev < kMaxDevices) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[dev], k, NT, sm);
+  });
   dim3 grid(a.n[1] / TY, a.n[2], a.L * ((a.emode == E_NODAL || a.emode == E_NOUT) ? 1 : a.nq));
-  k<<<grid, NT, sm, s>>>(a);
+  if (ahead) {
+    PassArgs<T> b = a;
+    b.pf_ahead = prefetch_distance((dev >= 0 && dev < kMaxDevices) ? occ[dev] : 0, 16);
+    k<<<grid, NT, sm, s>>>(b);
+  } else {
+    k<<<grid, NT, sm, s>>>(a);
+  }
   return cudaGetLastError();
 }
 // Tile variants of pass A: 0 default rows per block, 1 half, 2 double (threads
 // = the FFT's); 3 default rows and 4 half rows with one thread per load unit;
 // 5 (FP32, n_x >= 128, CG iterations) the pipelined persistent pass with
-// bulk-copied rows (pass3d_pipe.cuh); other modes of variant 5 use variant 0.
+// bulk-copied rows (pass3d_pipe.cuh); other modes of variant 5 use variant 0;
+// 6 variant 0 with the L2 prefetch of a later block's rows.
 template <typename T, int NX>
 cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4 && NX >= 128) {
@@ -586,12 +729,14 @@ cudaError_t launch_a_3d_n(const PassArgs<T>& a, cudaStream_t s) {
     if (a.var_a == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_a_3d_t<T, NX, tile_rows3<T>(2)>(a, s);
     if (a.var_a == 3) return launch_a_3d_t<T, NX, tile_rows3<T>(0), true>(a, s);
     if (a.var_a == 4) return launch_a_3d_t<T, NX, tile_rows3<T>(1), true>(a, s);
+    if (a.var_a == 6) return launch_a_3d_t<T, NX, tile_rows3<T>(0)>(a, s, true);
   }
   return launch_a_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
 }
 // Tile variants of pass E: 0 default rows per block, 1 half, 2 double; 3
 // (FP32, n_x >= 128, CG iterations, with the spectrum's tensor map) the
-// pipelined persistent pass (pass3d_pipe.cuh); other modes of 3 use 0.
+// pipelined persistent pass (pass3d_pipe.cuh); other modes of 3 use 0; 4
+// variant 0 with the L2 prefetch of a later block's spectrum tile and rows.
 template <typename T, int NX>
 cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) == 4 && NX >= 128) {
@@ -601,6 +746,7 @@ cudaError_t launch_e_3d_n(const PassArgs<T>& a, cudaStream_t s) {
   if constexpr (NX >= 64) {
     if (a.var_e == 1) return launch_e_3d_t<T, NX, tile_rows3<T>(1)>(a, s);
     if (a.var_e == 2 && a.n[1] >= tile_rows3<T>(2)) return launch_e_3d_t<T, NX, tile_rows3<T>(2)>(a, s);
+    if (a.var_e == 4) return launch_e_3d_t<T, NX, tile_rows3<T>(0)>(a, s, true);
   }
   return launch_e_3d_t<T, NX, tile_rows3<T>(0)>(a, s);
 }
@@ -611,12 +757,23 @@ cudaError_t launch_y_3d_v(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * TZB * FftSplit<NY, V>::LDO;
   auto k = pass_y_3d<T, NY, TZB, NT, FWD, V>;
   static DeviceOnce attr;
-  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
+  static int occ[kMaxDevices] = {0};
+  const int dev = current_device();
+  attr.run(dev, [&] {
+    set_smem_attrs(k, sm);
+    if (dev >= 0 && dev < kMaxDevices) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[dev], k, NT, sm);
+  });
   const bool din = (a.pmode == P_NODAL_IN || a.pmode == P_SOLVE);
   const bool dout = (a.pmode == P_NODAL_OUT || a.pmode == P_SOLVE);
   const int Cc = FWD ? (din ? 3 : a.m) : (dout ? 3 : a.m);
   dim3 grid(a.n[2] / TZB, a.kx, a.L * Cc);
-  k<<<grid, NT, sm, s>>>(a, Cc);
+  if (sizeof(T) == 4) {
+    PassArgs<T> b = a;
+    b.pf_ahead = prefetch_distance((dev >= 0 && dev < kMaxDevices) ? occ[dev] : 0, 2);
+    k<<<grid, NT, sm, s>>>(b, Cc);
+  } else {
+    k<<<grid, NT, sm, s>>>(a, Cc);
+  }
   return cudaGetLastError();
 }
 // Split variant of the y transforms (passes B and D): a.var_y.
@@ -640,9 +797,20 @@ cudaError_t launch_c_3d_v(const PassArgs<T>& a, cudaStream_t s) {
   const size_t sm = sizeof(cplx<T>) * 36 * pass_c_ld<T, NZ, V>();
   auto k = pass_c_3d<T, NZ, NT, V>;
   static DeviceOnce attr;
-  attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
+  static int occ[kMaxDevices] = {0};
+  const int dev = current_device();
+  attr.run(dev, [&] {
+    set_smem_attrs(k, sm);
+    if (dev >= 0 && dev < kMaxDevices) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[dev], k, NT, sm);
+  });
   dim3 grid(a.kx, a.n[1], a.L);
-  k<<<grid, NT, sm, s>>>(a);
+  if (sizeof(T) == 4) {
+    PassArgs<T> b = a;
+    b.pf_ahead = prefetch_distance((dev >= 0 && dev < kMaxDevices) ? occ[dev] : 0, 2);
+    k<<<grid, NT, sm, s>>>(b);
+  } else {
+    k<<<grid, NT, sm, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -513,7 +513,9 @@ int write_state(rve_s* h, int L) {
 // ---- autotuner: the schedule of the FFT passes --------------------------
 // Candidates per pass (rve_sched_candidates): pass A rows per block (default,
 // half, double) and one thread per load unit at the default and half rows;
-// pass E rows per block (default, half, double); the FFT split (radix
+// pass E rows per block (default, half, double); in 3D FP32 with n_x >= 128
+// also the pipelined persistent passes and the default tiles with the L2
+// prefetch of a later block's rows (A 5 and 6, E 3 and 4); the FFT split (radix
 // schedule) of pass C's axis; in 3D the split of the y axis (passes B and D,
 // timed together).  Each candidate is timed on the handle's own buffers
 // (operator-application modes on a zeroed field, 2 warm-up and 3 timed
@@ -544,8 +546,8 @@ int split_count(int n) {
 // Number of candidates of schedule entry `which` for a handle.
 int rve_sched_candidates(const rve_s* h, int which) {
   switch (which) {
-    case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 6 : h->n[0] >= 64 ? 5 : 3;
-    case 1: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128 && h->tm_ok) ? 4 : 3;
+    case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 7 : h->n[0] >= 64 ? 5 : 3;
+    case 1: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128 && h->tm_ok) ? 5 : 3;
     case 2: return split_count(h->n[h->dim - 1]);
     default: return h->dim == 3 ? split_count(h->n[1]) : 1;
   }

@@ -461,6 +461,16 @@ inline int current_device() {
   }
   return d;
 }
+// Streaming multiprocessors of the current device (queried once per device).
+inline int device_sm_count() {
+  static DeviceOnce once;
+  static int sms[kMaxDevices] = {0};
+  const int dev = current_device();
+  once.run(dev, [&] {
+    if (dev >= 0 && dev < kMaxDevices) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  });
+  return (dev >= 0 && dev < kMaxDevices && sms[dev] > 0) ? sms[dev] : 152;
+}
 
 // ------------------------------------------------------------ reductions
 template <int NT> __device__ __forceinline__ double block_sum(double v, double* red) {

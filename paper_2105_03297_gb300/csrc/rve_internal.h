@@ -64,11 +64,13 @@ template <typename T> struct PassArgs {
   int part_stride;
   int amode, emode, pmode;
   int cgphase;       // 1 inside the CG loop: passes skip load cases whose CG stopped
-  int var_a, var_e;  // tile variants of passes A (0..4) and E (0..2): see the launchers
+  int var_a, var_e;  // tile variants of passes A (0..6) and E (0..4): see the launchers
   int var_c, var_y;  // FFT split variants (FftSplit<N, V>) of pass C's axis and of passes B / D (3D)
   int comp_in;       // number of components in the spectrum for this pass (m or D)
   const void* tm_spec;  // host copy of the TMA tensor map of the first spectrum (3D FP32), or null
   int stall_copies;     // test hook: the pipelined passes issue no copies, so their bounded waits run out
+  int pf_ahead;      // 3D passes A and E: blocks ahead in launch order whose rows each block asks the TMA
+                     // unit to prefetch into L2 (tile variants A 6 and E 4), 0 = none
   int deriv;         // Deriv
 };
 

@@ -183,10 +183,10 @@ def test_every_tile_variant_gives_the_same_solution(dim):
         r.set_material(E, 0.3)
         r.solve(np.eye(ns), rel_tol=1e-11, max_iter=3000)
         var, ms = r.schedule()
-        assert var[0] in range(6) and var[1] in range(3) and var[2] in (0, 1) and var[3] in (0, 1)
+        assert var[0] in range(7) and var[1] in range(5) and var[2] in (0, 1) and var[3] in (0, 1)
         # candidate times are those of the last tuning of this handle (zero when the
         # choice came from the per-grid cache of an earlier handle)
-        assert len(ms) == 4 and all(len(m) == 6 and min(m) >= 0 for m in ms)
+        assert len(ms) == 4 and all(len(m) == r.SCHED_VARIANTS and min(m) >= 0 for m in ms)
 
 
 @pytest.mark.parametrize("n", [(64, 64), (64, 32, 16), (16, 128, 64)])

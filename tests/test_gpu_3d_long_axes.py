@@ -94,14 +94,16 @@ def test_solve_long_axis_matches_oracle(n, form, prec):
 def test_pipelined_passes_run_the_same_cg(n):
     """Tile variant 5 of the first pass and variant 3 of the last pass (persistent
     grids whose next tile's rows, and the last pass's spectrum tile, arrive by
-    TMA copies on an mbarrier while the current tile is transformed) run the same
-    CG as variants 0: two load cases solved together (per-slot partial sums)
-    give the same mean stresses to 1e-10, and the oracle's to 1e-9."""
+    TMA copies on an mbarrier while the current tile is transformed), and
+    variants 6 and 4 (the default tiles, each block asking for a later block's
+    rows and spectrum tile to be prefetched into L2), run the same CG as
+    variants 0: two load cases solved together (per-slot partial sums) give the
+    same mean stresses to 1e-10, and the oracle's to 1e-9."""
     from paper_2105_03297_gb300 import RVE
     E = lognormal(n, 95)
     Em = np.eye(6)[[0, 3]]
     S = {}
-    for va, ve in ((0, 0), (5, 0), (0, 3), (5, 3)):
+    for va, ve in ((0, 0), (5, 0), (0, 3), (5, 3), (6, 4), (6, 0), (0, 4)):
         with RVE(n, precision="mixed") as r:
             r.set_schedule(va, ve, 0, 0)
             r.set_material(E, 0.3)
@@ -109,7 +111,7 @@ def test_pipelined_passes_run_the_same_cg(n):
             assert code == 0, info
             assert r.schedule()[0][:2] == [va, ve]
             S[va, ve] = r.mean_stress()
-    for key in ((5, 0), (0, 3), (5, 3)):
+    for key in ((5, 0), (0, 3), (5, 3), (6, 4), (6, 0), (0, 4)):
         assert rel_max(S[key], S[0, 0]) < 1e-10, key
     if n == (256, 16, 16):
         S_ref, _ = _oracle(n)
