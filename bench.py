@@ -108,9 +108,35 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def strip_comments(src):
+    """C/C++ source without its comments and blank lines, each line's trailing
+    whitespace removed (string and character literals are kept as they are)."""
+    out = []
+    i, n = 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash():
-    """Short hash of the CUDA sources (csrc/): ties a stored ncu traffic
-    figure to the kernels it was measured on."""
+    """Short hash of the CUDA sources (csrc/) with their comments removed: ties
+    a stored ncu traffic figure to the code it was measured on."""
     import glob
     import hashlib
     h = hashlib.sha256()
@@ -119,8 +145,8 @@ def kernel_source_hash():
                    + glob.glob(os.path.join(csrc, "*.h")))
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -662,7 +662,9 @@ template <int A, int B> constexpr int max_i() { return A > B ? A : B; }
 //     at div 16 / 8 / 4 / 2 / 1;
 //   pass C (72 KB per block): 1.52 without, 1.55 / 1.53 / 1.47 / 1.41 / 1.43;
 //   pass D (32 KB per block, scattered z-chunks): 0.85 without, 0.83 / 0.82 /
-//     0.82 / 0.82 / 0.84.
+//     0.82 / 0.82 / 0.84;
+//   pass E (tile variant 4, 97 KB per block): 1.82 without, 1.80 at div 16, 8
+//     and 4, 1.87 at div 2 (the pipelined variant 3, 1.74, stays faster).
 inline int prefetch_distance(int occ, int div) {
   const int d = occ * device_sm_count() / div;
   return d > 1 ? d : 1;

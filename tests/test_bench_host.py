@@ -44,6 +44,13 @@ def test_traffic_rows_follow_the_kernel_hash(tmp_path):
     assert bench.measured_traffic("w", "stress", "pass_a", 3, path=str(p)) is None
 
 
+def test_source_hash_ignores_comments():
+    src = 'int a = 1; // note\n/* block\n comment */ const char* s = "x // y /* z */";\nchar q = \'"\';\n\n  \nint b;'
+    assert bench.strip_comments(src) == 'int a = 1;\n const char* s = "x // y /* z */";\nchar q = \'"\';\nint b;'
+    assert bench.strip_comments("a; // one\na;") == bench.strip_comments("a;\na; // two")
+    assert bench.strip_comments("a = 1;") != bench.strip_comments("a = 2;")
+
+
 def test_scope_model_bytes():
     # 256^3, FP32 fields and spectra: (8 * 4 + 8 * 4) * 36 * N + 4 N = 38.7 GB per CG iteration
     N = 256 ** 3
