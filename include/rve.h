@@ -180,7 +180,9 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  *      variant 0 whose blocks each ask for a later block's rows to be
  *      prefetched into L2 (a hint: no wait, same arithmetic).  A bounded
  *      device-side wait of variant 5 that gives up makes the solve return
- *      RVE_ERR_TIMEOUT;
+ *      RVE_ERR_TIMEOUT.  In 2D with RVE_MIXED and n_x = 1024, 5 is half rows
+ *      per block with each 32-point register FFT of the x transform spread
+ *      over a pair of lanes (fewer registers, three blocks per SM);
  *  [1] the last pass (inverse x FFT + CG update): 0 default rows, 1 half, 2 double;
  *      in 3D with RVE_MIXED and n_x >= 128 also 3, a persistent pipelined
  *      pass whose next spectrum tile arrives by one tensor copy (same
@@ -192,7 +194,8 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  *      128 = 4 x 32, 256 = 8 x 32; lengths 512 and 1024 have only split 0);
  *  [3] in 3D the same choice for the y transforms (0 or 1); 0 in 2D.
  * -1 = choose by timing the candidates on the handle's buffers at the next
- * solve (the default; the choice is cached per grid and precision for the
+ * solve, with that solve's load cases (at most 8) (the default; the choice is
+ * cached per grid, precision and number of load cases timed for the
  * process).  rve_set_schedule rejects a variant the grid does not have.
  * rve_schedule also returns the measured candidate times
  * candidate_ms[RVE_SCHED_PASSES][RVE_SCHED_VARIANTS] (0 where a candidate does

@@ -212,8 +212,11 @@ template <typename T, int NT> __host__ __device__ constexpr int pass_a2_min_bloc
 
 // NT is either the FFT's thread count or (tile variants 3, 4) the number of
 // load units of the tile, so that every thread streams exactly one unit.
-template <typename T, int NX, int TY, int NT>
-__global__ void __launch_bounds__(NT, pass_a2_min_blocks<T, NT>()) pass_a_2d(PassArgs<T> a) {
+// PAIR (n_x = 1024, tile variant 5): the x transform spreads each 32-point
+// register FFT over a lane pair (smem_fft_pair), NT = 2 x 32 per transform,
+// three blocks per SM.
+template <typename T, int NX, int TY, int NT, bool PAIR = false>
+__global__ void __launch_bounds__(NT, PAIR ? 3 : pass_a2_min_blocks<T, NT>()) pass_a_2d(PassArgs<T> a) {
   using C = cplx<T>;
   constexpr int NP = TY / 2;
   constexpr int GS = 3;
@@ -234,10 +237,13 @@ __global__ void __launch_bounds__(NT, pass_a2_min_blocks<T, NT>()) pass_a_2d(Pas
   T beta = 0, alpha_prev = 0;
   bool use_old = false;
   if (a.amode == A_CG) { beta = (T)cg->beta; alpha_prev = (T)cg->alpha; use_old = cg->it > 0; }
-  const T acc = pass_a_load<T, NX, TY, GS, NT, LD>(a, buf, l, c0, (int64_t)y0 * NX, nodal, beta, alpha_prev,
-                                                   use_old);
+  // the lane-pair variant runs three blocks per SM: units of two columns (8-byte
+  // loads, as in 3D) keep the load phase within its registers
+  const T acc = pass_a_load<T, NX, TY, GS, NT, LD, PAIR ? 2 : Vec16<T>::n>(a, buf, l, c0, (int64_t)y0 * NX, nodal,
+                                                                          beta, alpha_prev, use_old);
   __syncthreads();
-  smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
+  if constexpr (PAIR) smem_fft_pair<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
+  else smem_fft<T, NX, GS * NP, LD, NT, -1>(buf, a.tw[0]);
   pass_a_store<T, NX, TY, NT, LD>(buf, nodal ? 2 : 3, a.spec + (((int64_t)l * a.m + c0) * KX) * ny + y0,
                                   (int64_t)KX * ny, ny);
 
@@ -614,13 +620,14 @@ template <typename T> constexpr int tile_rows(int v) {
   return v == 1 ? Tile2D<T>::TY / 2 : v == 2 ? Tile2D<T>::TY * 2 : Tile2D<T>::TY;
 }
 
-template <typename T, int NX, int TY, bool BY_UNITS = false>
+template <typename T, int NX, int TY, bool BY_UNITS = false, bool PAIR = false>
 cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int NF = fft_threads<NX, 3 * (TY / 2)>();
+  constexpr int NF = PAIR ? 2 * 32 * 3 * (TY / 2) : fft_threads<NX, 3 * (TY / 2)>();
   constexpr int NU = ((TY / 2) * (NX / Vec16<T>::n) + 31) / 32 * 32;   // load units of a tile
   constexpr int NT = (BY_UNITS && NU > NF && NU <= 1024) ? NU : NF;
+  static_assert(NT <= 1024, "threads per block");
   const size_t sm = sizeof(cplx<T>) * 3 * (TY / 2) * ae_ld<NX>();
-  auto k = pass_a_2d<T, NX, TY, NT>;
+  auto k = pass_a_2d<T, NX, TY, NT, PAIR>;
   static DeviceOnce attr;
   attr.run(current_device(), [&] { set_smem_attrs(k, sm); });
   dim3 grid(a.n[1] / TY, a.amode == A_NODAL ? 1 : a.nq, a.L);
@@ -638,8 +645,14 @@ cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
   k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
+// Tile variants of the 2D pass A: 0 default rows per block, 1 half, 2 double
+// (threads = the FFT's); 3 default rows and 4 half rows with one thread per
+// load unit; 5 (FP32, n_x = 1024) half rows with the lane-pair x transform.
 template <typename T, int NX>
 cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
+  if constexpr (NX == 1024 && sizeof(T) == 4) {
+    if (a.var_a == 5) return launch_a_2d_t<T, NX, tile_rows<T>(1), false, true>(a, s);
+  }
   if constexpr (NX >= 64) {
     if (a.var_a == 1) return launch_a_2d_t<T, NX, tile_rows<T>(1)>(a, s);
     if (a.var_a == 2 && a.n[1] >= tile_rows<T>(2)) return launch_a_2d_t<T, NX, tile_rows<T>(2)>(a, s);
@@ -648,6 +661,9 @@ cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   }
   return launch_a_2d_t<T, NX, tile_rows<T>(0)>(a, s);
 }
+// Tile variants of the 2D pass E: 0 default rows per block, 1 half, 2 double.
+// (The lane-pair x transform of pass A's variant 5 made pass E slower at
+// 1024^2: 0.091 against 0.083 ms per iteration for three load cases.)
 template <typename T, int NX>
 cudaError_t launch_e_2d_n(const PassArgs<T>& a, cudaStream_t s) {
   if constexpr (NX >= 64) {

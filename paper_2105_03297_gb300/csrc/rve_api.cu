@@ -515,17 +515,19 @@ int write_state(rve_s* h, int L) {
 // half, double) and one thread per load unit at the default and half rows;
 // pass E rows per block (default, half, double); in 3D FP32 with n_x >= 128
 // also the pipelined persistent passes and the default tiles with the L2
-// prefetch of a later block's rows (A 5 and 6, E 3 and 4); the FFT split (radix
+// prefetch of a later block's rows (A 5 and 6, E 3 and 4); in 2D FP32 with
+// n_x = 1024 also pass A with the lane-pair x transform (A 5); the FFT split (radix
 // schedule) of pass C's axis; in 3D the split of the y axis (passes B and D,
 // timed together).  Each candidate is timed on the handle's own buffers
-// (operator-application modes on a zeroed field, 2 warm-up and 3 timed
-// launches, CUDA events on the handle's stream), passes in the order A, E, C,
-// B/D with the winners of the earlier ones, and the fastest is kept; choices
-// are cached per (dimension, grid, precision) for the process.
+// (CG-iteration modes on zeroed fields of the solve's load cases, at most
+// kTuneMaxL; 2 warm-up and 3 timed launches, CUDA events on the handle's
+// stream), passes in the order A, E, C, B/D with the winners of the earlier
+// ones, and the fastest is kept; choices are cached per (dimension, grid,
+// precision, load cases timed) for the process.
 struct TuneKey {
-  int dim, n0, n1, n2, tsize;
+  int dim, n0, n1, n2, tsize, nl;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dim, n0, n1, n2, tsize) < std::tie(o.dim, o.n0, o.n1, o.n2, o.tsize);
+    return std::tie(dim, n0, n1, n2, tsize, nl) < std::tie(o.dim, o.n0, o.n1, o.n2, o.tsize, o.nl);
   }
 };
 std::map<TuneKey, std::array<int, RVE_SCHED_PASSES>> g_tuned;
@@ -546,15 +548,22 @@ int split_count(int n) {
 // Number of candidates of schedule entry `which` for a handle.
 int rve_sched_candidates(const rve_s* h, int which) {
   switch (which) {
-    case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 7 : h->n[0] >= 64 ? 5 : 3;
+    case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 7
+                 : (h->dim == 2 && h->tsize == 4 && h->n[0] == 1024) ? 6 : h->n[0] >= 64 ? 5 : 3;
     case 1: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128 && h->tm_ok) ? 5 : 3;
     case 2: return split_count(h->n[h->dim - 1]);
     default: return h->dim == 3 ? split_count(h->n[1]) : 1;
   }
 }
 
-template <typename T> int autotune(rve_s* h) {
-  const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], (int)h->tsize};
+// Load cases the candidates are timed with: those of the solve that asks for
+// the tuning (the grids of the passes scale with them, and with them how full
+// the last wave of blocks is), at most kTuneMaxL.
+constexpr int kTuneMaxL = 8;
+
+template <typename T> int autotune(rve_s* h, int L) {
+  const int Lt = L < 1 ? 1 : (L > kTuneMaxL ? kTuneMaxL : L);
+  const TuneKey key{h->dim, h->n[0], h->n[1], h->n[2], (int)h->tsize, Lt};
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tuned.find(key);
@@ -566,19 +575,21 @@ template <typename T> int autotune(rve_s* h) {
   }
   // passes A and E are timed in their CG-iteration modes (A: direction update,
   // deferred x update, material, x FFT, <p, C p>; E: inverse x FFT, r update,
-  // <r, r>) on zeroed vectors of one load case; the CG state they finalise is
+  // <r, r>) on zeroed vectors of Lt load cases; the CG state they finalise is
   // reset by the solve that follows
   const size_t fld = (size_t)h->m * h->N * h->tsize;
   CK(cudaMemsetAsync(h->fbuf, 0, fld, h->stream));
-  CK(cudaMemsetAsync(h->r, 0, fld, h->stream));
-  CK(cudaMemsetAsync(h->p, 0, fld, h->stream));
-  CK(cudaMemsetAsync(h->x, 0, fld, h->stream));
-  std::memset(h->cg_h, 0, sizeof(CgState));
-  h->cg_h[0].active = 1;
-  h->cg_h[0].it = 1;
-  int rc = write_state(h, 1);
+  CK(cudaMemsetAsync(h->r, 0, fld * Lt, h->stream));
+  CK(cudaMemsetAsync(h->p, 0, fld * Lt, h->stream));
+  CK(cudaMemsetAsync(h->x, 0, fld * Lt, h->stream));
+  std::memset(h->cg_h, 0, sizeof(CgState) * Lt);
+  for (int l = 0; l < Lt; ++l) {
+    h->cg_h[l].active = 1;
+    h->cg_h[l].it = 1;
+  }
+  int rc = write_state(h, Lt);
   if (rc) return rc;
-  PassArgs<T> a = pass_args<T>(h, 1, h->u, h->emac_d);
+  PassArgs<T> a = pass_args<T>(h, Lt, h->u, h->emac_d);
   a.cgphase = 0; a.amode = A_CG; a.pmode = P_G; a.emode = E_CG;
   a.in = (const T*)h->fbuf; a.out = (T*)h->x;
   a.var_a = a.var_e = a.var_c = a.var_y = 0;
@@ -1638,7 +1649,7 @@ int rve_solve(rve_t h, const double* E_macro, int L, double rel_tol, int max_ite
   int rc = ensure_capacity(h, L);
   if (rc) return rc;
   if (h->var[0] < 0 || h->var[1] < 0 || h->var[2] < 0 || h->var[3] < 0) {
-    rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
+    rc = (h->precision == RVE_MIXED) ? autotune<float>(h, L) : autotune<double>(h, L);
     if (rc) return rc;
   }
   const int st = (h->deriv != D_FE)
@@ -2079,7 +2090,7 @@ int rve_batch_solve(rve_batch_t b, const double* E_macro, int L, double rel_tol,
     int rc = ensure_capacity(h, Lg);
     if (rc) return rc;
     if (h->var[0] < 0 || h->var[1] < 0 || h->var[2] < 0 || h->var[3] < 0) {
-      rc = (h->precision == RVE_MIXED) ? autotune<float>(h) : autotune<double>(h);
+      rc = (h->precision == RVE_MIXED) ? autotune<float>(h, Lg) : autotune<double>(h, Lg);
       if (rc) return rc;
     }
   }

@@ -287,6 +287,156 @@ __device__ __forceinline__ void smem_fft(cplx<T>* buf, const cplx<T>* __restrict
   __syncthreads();
 }
 
+// 32-point FFT (sign S, natural order in and out) of one sequence held by the
+// lane pair (q, q + 16) of a warp: the lane with h = 0 holds the even-indexed
+// inputs x[2 m], the lane with h = 1 the odd-indexed x[2 m + 1] (m < 16), in
+// v.  Each lane transforms its 16 points; the odd lane twiddles its outputs
+// O_k by w^k = exp(S 2 pi i k / 32); one exchange per k gives lane h the
+// outputs X[16 h + k] = E_k +- w^k O_k in v[k] (the last radix-2
+// decimation-in-time stage of fft_reg<32>, with the same twiddle constants).
+// Every lane of the warp must call it: it shuffles over the full warp.
+template <int S, typename C>
+__device__ __forceinline__ void fft_reg_pair32(C* v, int h) {
+  using T = decltype(v[0].x);
+  fft_reg<16, S>(v);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    C t = v[k];
+    if (k == 8) {
+      t = cmul_i<S>(v[k]);
+    } else if (k == 4 || k == 12) {
+      const T c = (T)kCos32(4);
+      const T sx = (k == 4) ? (T)1 : (T)-1;
+      const T sy = (T)S;
+      t.x = c * (sx * v[k].x - sy * v[k].y);
+      t.y = c * (sx * v[k].y + sy * v[k].x);
+    } else if (k != 0) {
+      C w;
+      w.x = (T)kCos32(k);
+      w.y = (T)(S * kSin32(k));
+      t = cmul(v[k], w);
+    }
+    if (!h) t = v[k];                 // the even lane sends E_k, the odd lane w^k O_k
+    C o;
+    o.x = __shfl_xor_sync(0xffffffffu, t.x, 16);
+    o.y = __shfl_xor_sync(0xffffffffu, t.y, 16);
+    v[k] = h ? csub(o, t) : cadd(t, o);
+  }
+}
+
+// Steps of the four-step FFT for N = 32 x 32 (1024) with every 32-point
+// register FFT spread over a lane pair (fft_reg_pair32): half the registers
+// per thread and twice the threads per transform.  Work items of both steps
+// are pairs, 16 per warp, numbered across the block ((b, n1) in step 1,
+// (b, k2) in step 2, the second index fastest), so that the 16 lanes of each
+// half-warp touch consecutive shared-memory columns; the steps are separated
+// by block-wide barriers.  NT is a multiple of 32.
+template <int N, int NB, int NT> struct FftPairItems {
+  static constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
+  static_assert(N1 == 32 && N2 == 32, "lane-pair transforms need the 32 x 32 split");
+  static_assert(NT % 32 == 0, "whole warps");
+  static constexpr int P = NT / 2;            // pairs per round of the block
+  static constexpr int W = NB * 32;           // pairs per step
+  static constexpr int I = (W + P - 1) / P;   // rounds
+};
+
+// Step 1 (in place on buf, ends with a barrier): for every pair (b, n1), the
+// 32-point FFT over n2 of x[n1 + 32 n2], twiddled by exp(S 2 pi i n1 k2 / N)
+// and stored transposed with the padded stride 33.  The caller must
+// __syncthreads() before.
+template <typename T, int N, int NB, int LD, int NT, int S>
+__device__ __forceinline__ void fft_pair_step1(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  using It = FftPairItems<N, NB, NT>;
+  constexpr int N1 = It::N1, N2 = It::N2;
+  static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
+  const int lane = threadIdx.x & 31, h = lane >> 4;
+  const int p0 = (threadIdx.x >> 5) * 16 + (lane & 15);
+  C v[It::I][16];
+#pragma unroll
+  for (int i = 0; i < It::I; ++i) {
+    const int p = p0 + i * It::P;
+    if (p < It::W) {
+      const C* src = buf + (p / N1) * LD + p % N1;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[i][m] = src[(2 * m + h) * N1];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[i][m] = mkc<T>(0, 0);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < It::I; ++i) {
+    const int p = p0 + i * It::P;
+    fft_reg_pair32<S>(v[i], h);
+    if (p < It::W) {
+      const int n1 = p % N1;
+      C* dst = buf + (p / N1) * LD + n1;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int k2 = 16 * h + k;
+        C t = v[i][k];
+        if (k2 > 0 && n1 > 0) {
+          C w = __ldg(tw + n1 * k2);
+          if (S > 0) w.y = -w.y;
+          t = cmul(t, w);
+        }
+        dst[k2 * (N1 + 1)] = t;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Step 2: for every pair (b, k2), the 32-point FFT over n1 of the transposed
+// row; lane h of the pair ends with the outputs X[k2 + 32 k1], k1 = 16 h + k
+// (k < 16), in v[k] and hands them to out(b, k2, h, v): written back to buf
+// by smem_fft_pair, passed to the caller's store by the last passes.
+template <typename T, int N, int NB, int LD, int NT, int S, bool TO_SMEM, class Out>
+__device__ __forceinline__ void fft_pair_step2(cplx<T>* buf, const Out& out) {
+  using C = cplx<T>;
+  using It = FftPairItems<N, NB, NT>;
+  constexpr int N1 = It::N1, N2 = It::N2;
+  const int lane = threadIdx.x & 31, h = lane >> 4;
+  const int p0 = (threadIdx.x >> 5) * 16 + (lane & 15);
+  C v[It::I][16];
+#pragma unroll
+  for (int i = 0; i < It::I; ++i) {
+    const int p = p0 + i * It::P;
+    if (p < It::W) {
+      const C* src = buf + (p / N2) * LD + (p % N2) * (N1 + 1);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[i][m] = src[2 * m + h];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[i][m] = mkc<T>(0, 0);
+    }
+  }
+  if constexpr (TO_SMEM) __syncthreads();
+#pragma unroll
+  for (int i = 0; i < It::I; ++i) {
+    const int p = p0 + i * It::P;
+    fft_reg_pair32<S>(v[i], h);
+    if (p < It::W) out(p / N2, p % N2, h, v[i]);
+  }
+}
+
+// smem_fft for N = 1024 with lane-pair register FFTs (in place, natural order;
+// the caller must __syncthreads() before; ends with a barrier).
+template <typename T, int N, int NB, int LD, int NT, int S>
+__device__ __forceinline__ void smem_fft_pair(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  fft_pair_step1<T, N, NB, LD, NT, S>(buf, tw);
+  auto to_buf = [&](int b, int k2, int h, const C* v) {
+    C* dst = buf + b * LD + k2;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dst[(16 * h + k) * FftSplit<N>::N2] = v[k];
+  };
+  fft_pair_step2<T, N, NB, LD, NT, S, true>(buf, to_buf);
+  __syncthreads();
+}
+
 // Four-step FFT with caller-supplied input and output (same algorithm as
 // smem_fft): step 1 reads its inputs through load(b, n) (n = n1 + N1 n2), step 2
 // hands every output to store(b, k, value) (k = k2 + N2 k1).  The middle

@@ -212,6 +212,33 @@ def test_every_fft_schedule_gives_the_same_operator(n):
             assert np.abs(q - ref).max() <= 2e-5 * np.abs(ref).max(), sch
 
 
+def test_lane_pair_transform_variant_at_1024():
+    """Tile variant 5 of the first pass at n_x = 1024 (each 32-point register FFT
+    of the x transform spread over a lane pair) applies the same operator as the
+    oracle (FP32, to 2e-5 of the field maximum) and runs the same CG as
+    variant 0 (three load cases, C_eff to 1e-10, and the oracle's to 1e-9)."""
+    from paper_2105_03297_gb300 import RVE
+    n = (1024, 32)
+    E = lognormal(n, 64)
+    P = Problem(n, E, 0.3)
+    p = np.random.default_rng(65).standard_normal((P.m,) + E.shape).astype(np.float32).astype(np.float64)
+    ref = P.operator(p)
+    Cs = {}
+    for va, ve in ((0, 0), (5, 0)):
+        with RVE(n, precision="mixed") as r:
+            r.set_schedule(va, ve)
+            r.set_material(E, 0.3)
+            assert r.schedule()[0][:2] == [va, ve]
+            q = r.apply_operator(p.reshape(P.m, -1)).reshape(ref.shape)
+            assert np.abs(q - ref).max() <= 2e-5 * np.abs(ref).max(), (va, ve)
+            code, info = r.solve(np.eye(3), rel_tol=1e-12, max_iter=4000)
+            assert code == 0, info
+            Cs[va, ve] = r.effective_tangent()
+    assert rel_max(Cs[5, 0], Cs[0, 0]) < 1e-10
+    C_ref, _, _ = P.effective_tangent(np.eye(3), tol=1e-13)
+    assert rel_max(Cs[5, 0], C_ref) < 1e-9
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_anisotropic_voxels(prec):
     """Cell lengths enter through the voxel sizes h_a = L_a / n_a (Appendix A)."""
