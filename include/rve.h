@@ -180,9 +180,9 @@ int rve_apply_operator(rve_t h, const void* p, void* q, int apply_material, int 
  *      variant 0 whose blocks each ask for a later block's rows to be
  *      prefetched into L2 (a hint: no wait, same arithmetic).  A bounded
  *      device-side wait of variant 5 that gives up makes the solve return
- *      RVE_ERR_TIMEOUT.  In 2D with RVE_MIXED and n_x = 1024, 5 is half rows
- *      per block with each 32-point register FFT of the x transform spread
- *      over a pair of lanes (fewer registers, three blocks per SM);
+ *      RVE_ERR_TIMEOUT.  In 2D with RVE_MIXED and n_x = 512 or 1024, 5 is the
+ *      x transform with each 32-point register FFT spread over a pair of
+ *      lanes (fewer registers, three blocks per SM);
  *  [1] the last pass (inverse x FFT + CG update): 0 default rows, 1 half, 2 double;
  *      in 3D with RVE_MIXED and n_x >= 128 also 3, a persistent pipelined
  *      pass whose next spectrum tile arrives by one tensor copy (same

@@ -212,9 +212,9 @@ template <typename T, int NT> __host__ __device__ constexpr int pass_a2_min_bloc
 
 // NT is either the FFT's thread count or (tile variants 3, 4) the number of
 // load units of the tile, so that every thread streams exactly one unit.
-// PAIR (n_x = 1024, tile variant 5): the x transform spreads each 32-point
-// register FFT over a lane pair (smem_fft_pair), NT = 2 x 32 per transform,
-// three blocks per SM.
+// PAIR (n_x = 512 or 1024, tile variant 5): the x transform spreads each
+// 32-point register FFT of its first step over a lane pair (smem_fft_pair),
+// NT = 2 N1 per transform, three blocks per SM.
 template <typename T, int NX, int TY, int NT, bool PAIR = false>
 __global__ void __launch_bounds__(NT, PAIR ? 3 : pass_a2_min_blocks<T, NT>()) pass_a_2d(PassArgs<T> a) {
   using C = cplx<T>;
@@ -622,7 +622,7 @@ template <typename T> constexpr int tile_rows(int v) {
 
 template <typename T, int NX, int TY, bool BY_UNITS = false, bool PAIR = false>
 cudaError_t launch_a_2d_t(const PassArgs<T>& a, cudaStream_t s) {
-  constexpr int NF = PAIR ? 2 * 32 * 3 * (TY / 2) : fft_threads<NX, 3 * (TY / 2)>();
+  constexpr int NF = PAIR ? 2 * FftSplit<NX>::N1 * 3 * (TY / 2) : fft_threads<NX, 3 * (TY / 2)>();
   constexpr int NU = ((TY / 2) * (NX / Vec16<T>::n) + 31) / 32 * 32;   // load units of a tile
   constexpr int NT = (BY_UNITS && NU > NF && NU <= 1024) ? NU : NF;
   static_assert(NT <= 1024, "threads per block");
@@ -647,11 +647,12 @@ cudaError_t launch_e_2d_t(const PassArgs<T>& a, cudaStream_t s) {
 }
 // Tile variants of the 2D pass A: 0 default rows per block, 1 half, 2 double
 // (threads = the FFT's); 3 default rows and 4 half rows with one thread per
-// load unit; 5 (FP32, n_x = 1024) half rows with the lane-pair x transform.
+// load unit; 5 (FP32, n_x = 512 or 1024) the lane-pair x transform with 384
+// threads (default rows at 512, half rows at 1024).
 template <typename T, int NX>
 cudaError_t launch_a_2d_n(const PassArgs<T>& a, cudaStream_t s) {
-  if constexpr (NX == 1024 && sizeof(T) == 4) {
-    if (a.var_a == 5) return launch_a_2d_t<T, NX, tile_rows<T>(1), false, true>(a, s);
+  if constexpr ((NX == 512 || NX == 1024) && sizeof(T) == 4) {
+    if (a.var_a == 5) return launch_a_2d_t<T, NX, NX == 1024 ? tile_rows<T>(1) : tile_rows<T>(0), false, true>(a, s);
   }
   if constexpr (NX >= 64) {
     if (a.var_a == 1) return launch_a_2d_t<T, NX, tile_rows<T>(1)>(a, s);

@@ -516,7 +516,7 @@ int write_state(rve_s* h, int L) {
 // pass E rows per block (default, half, double); in 3D FP32 with n_x >= 128
 // also the pipelined persistent passes and the default tiles with the L2
 // prefetch of a later block's rows (A 5 and 6, E 3 and 4); in 2D FP32 with
-// n_x = 1024 also pass A with the lane-pair x transform (A 5); the FFT split (radix
+// n_x = 512 or 1024 also pass A with the lane-pair x transform (A 5); the FFT split (radix
 // schedule) of pass C's axis; in 3D the split of the y axis (passes B and D,
 // timed together).  Each candidate is timed on the handle's own buffers
 // (CG-iteration modes on zeroed fields of the solve's load cases, at most
@@ -549,7 +549,7 @@ int split_count(int n) {
 int rve_sched_candidates(const rve_s* h, int which) {
   switch (which) {
     case 0: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128) ? 7
-                 : (h->dim == 2 && h->tsize == 4 && h->n[0] == 1024) ? 6 : h->n[0] >= 64 ? 5 : 3;
+                 : (h->dim == 2 && h->tsize == 4 && h->n[0] >= 512) ? 6 : h->n[0] >= 64 ? 5 : 3;
     case 1: return (h->dim == 3 && h->tsize == 4 && h->n[0] >= 128 && h->tm_ok) ? 5 : 3;
     case 2: return split_count(h->n[h->dim - 1]);
     default: return h->dim == 3 ? split_count(h->n[1]) : 1;

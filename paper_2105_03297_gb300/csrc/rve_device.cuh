@@ -324,25 +324,30 @@ __device__ __forceinline__ void fft_reg_pair32(C* v, int h) {
   }
 }
 
-// Steps of the four-step FFT for N = 32 x 32 (1024) with every 32-point
-// register FFT spread over a lane pair (fft_reg_pair32): half the registers
-// per thread and twice the threads per transform.  Work items of both steps
-// are pairs, 16 per warp, numbered across the block ((b, n1) in step 1,
-// (b, k2) in step 2, the second index fastest), so that the 16 lanes of each
+// Steps of the four-step FFT for N = N1 x 32 (N1 = 32: 1024, N1 = 16: 512)
+// with every 32-point register FFT of step 1 spread over a lane pair
+// (fft_reg_pair32): half the registers per thread and 2 N1 threads per
+// transform.  Step 1 items are pairs (b, n1), 16 per warp (lanes q and q + 16
+// form pair q); step 2 items are pairs (b, k2) again when N1 = 32 and single
+// lanes (b, k2) with a 16-point register FFT when N1 = 16.  Items are numbered
+// across the block, the second index fastest, so that the 16 lanes of each
 // half-warp touch consecutive shared-memory columns; the steps are separated
 // by block-wide barriers.  NT is a multiple of 32.
 template <int N, int NB, int NT> struct FftPairItems {
   static constexpr int N1 = FftSplit<N>::N1, N2 = FftSplit<N>::N2;
-  static_assert(N1 == 32 && N2 == 32, "lane-pair transforms need the 32 x 32 split");
+  static_assert(N2 == 32 && (N1 == 32 || N1 == 16), "lane-pair transforms need N2 = 32 and N1 = 16 or 32");
   static_assert(NT % 32 == 0, "whole warps");
-  static constexpr int P = NT / 2;            // pairs per round of the block
-  static constexpr int W = NB * 32;           // pairs per step
-  static constexpr int I = (W + P - 1) / P;   // rounds
+  static constexpr bool PAIR2 = (N1 == 32);    // step 2 on lane pairs too
+  static constexpr int P = NT / 2;             // pairs per round of the block
+  static constexpr int W1 = NB * N1;           // step-1 pairs
+  static constexpr int I1 = (W1 + P - 1) / P;  // step-1 rounds
+  static constexpr int W2 = NB * N2;           // step-2 items (pairs or lanes)
+  static constexpr int I2 = PAIR2 ? (W2 + P - 1) / P : (W2 + NT - 1) / NT;
 };
 
 // Step 1 (in place on buf, ends with a barrier): for every pair (b, n1), the
-// 32-point FFT over n2 of x[n1 + 32 n2], twiddled by exp(S 2 pi i n1 k2 / N)
-// and stored transposed with the padded stride 33.  The caller must
+// 32-point FFT over n2 of x[n1 + N1 n2], twiddled by exp(S 2 pi i n1 k2 / N)
+// and stored transposed with the padded stride N1 + 1.  The caller must
 // __syncthreads() before.
 template <typename T, int N, int NB, int LD, int NT, int S>
 __device__ __forceinline__ void fft_pair_step1(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
@@ -352,11 +357,11 @@ __device__ __forceinline__ void fft_pair_step1(cplx<T>* buf, const cplx<T>* __re
   static_assert(LD >= N + N2, "leading dimension too small for the padded transpose");
   const int lane = threadIdx.x & 31, h = lane >> 4;
   const int p0 = (threadIdx.x >> 5) * 16 + (lane & 15);
-  C v[It::I][16];
+  C v[It::I1][16];
 #pragma unroll
-  for (int i = 0; i < It::I; ++i) {
+  for (int i = 0; i < It::I1; ++i) {
     const int p = p0 + i * It::P;
-    if (p < It::W) {
+    if (p < It::W1) {
       const C* src = buf + (p / N1) * LD + p % N1;
 #pragma unroll
       for (int m = 0; m < 16; ++m) v[i][m] = src[(2 * m + h) * N1];
@@ -367,10 +372,10 @@ __device__ __forceinline__ void fft_pair_step1(cplx<T>* buf, const cplx<T>* __re
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < It::I; ++i) {
+  for (int i = 0; i < It::I1; ++i) {
     const int p = p0 + i * It::P;
     fft_reg_pair32<S>(v[i], h);
-    if (p < It::W) {
+    if (p < It::W1) {
       const int n1 = p % N1;
       C* dst = buf + (p / N1) * LD + n1;
 #pragma unroll
@@ -389,41 +394,63 @@ __device__ __forceinline__ void fft_pair_step1(cplx<T>* buf, const cplx<T>* __re
   __syncthreads();
 }
 
-// Step 2: for every pair (b, k2), the 32-point FFT over n1 of the transposed
-// row; lane h of the pair ends with the outputs X[k2 + 32 k1], k1 = 16 h + k
-// (k < 16), in v[k] and hands them to out(b, k2, h, v): written back to buf
-// by smem_fft_pair, passed to the caller's store by the last passes.
+// Step 2: for every (b, k2), the N1-point FFT over n1 of the transposed row.
+// With N1 = 32 a lane pair shares it and lane h ends with the outputs
+// X[k2 + 32 k1], k1 = 16 h + k; with N1 = 16 one lane holds all 16 (h = 0).
+// The outputs, v[k] for k < 16, go to out(b, k2, h, v): written back to buf by
+// smem_fft_pair, passed to the caller's store by a last pass.
 template <typename T, int N, int NB, int LD, int NT, int S, bool TO_SMEM, class Out>
 __device__ __forceinline__ void fft_pair_step2(cplx<T>* buf, const Out& out) {
   using C = cplx<T>;
   using It = FftPairItems<N, NB, NT>;
   constexpr int N1 = It::N1, N2 = It::N2;
-  const int lane = threadIdx.x & 31, h = lane >> 4;
-  const int p0 = (threadIdx.x >> 5) * 16 + (lane & 15);
-  C v[It::I][16];
+  C v[It::I2][16];
+  if constexpr (It::PAIR2) {
+    const int lane = threadIdx.x & 31, h = lane >> 4;
+    const int p0 = (threadIdx.x >> 5) * 16 + (lane & 15);
 #pragma unroll
-  for (int i = 0; i < It::I; ++i) {
-    const int p = p0 + i * It::P;
-    if (p < It::W) {
-      const C* src = buf + (p / N2) * LD + (p % N2) * (N1 + 1);
+    for (int i = 0; i < It::I2; ++i) {
+      const int p = p0 + i * It::P;
+      if (p < It::W2) {
+        const C* src = buf + (p / N2) * LD + (p % N2) * (N1 + 1);
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[i][m] = src[2 * m + h];
-    } else {
+        for (int m = 0; m < 16; ++m) v[i][m] = src[2 * m + h];
+      } else {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[i][m] = mkc<T>(0, 0);
+        for (int m = 0; m < 16; ++m) v[i][m] = mkc<T>(0, 0);
+      }
     }
-  }
-  if constexpr (TO_SMEM) __syncthreads();
+    if constexpr (TO_SMEM) __syncthreads();
 #pragma unroll
-  for (int i = 0; i < It::I; ++i) {
-    const int p = p0 + i * It::P;
-    fft_reg_pair32<S>(v[i], h);
-    if (p < It::W) out(p / N2, p % N2, h, v[i]);
+    for (int i = 0; i < It::I2; ++i) {
+      const int p = p0 + i * It::P;
+      fft_reg_pair32<S>(v[i], h);
+      if (p < It::W2) out(p / N2, p % N2, h, v[i]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < It::I2; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if (it < It::W2) {
+        const C* src = buf + (it / N2) * LD + (it % N2) * (N1 + 1);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[i][m] = src[m];
+      }
+    }
+    if constexpr (TO_SMEM) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < It::I2; ++i) {
+      const int it = threadIdx.x + i * NT;
+      if (it < It::W2) {
+        fft_reg<16, S>(v[i]);
+        out(it / N2, it % N2, 0, v[i]);
+      }
+    }
   }
 }
 
-// smem_fft for N = 1024 with lane-pair register FFTs (in place, natural order;
-// the caller must __syncthreads() before; ends with a barrier).
+// smem_fft for N = 512 or 1024 with lane-pair register FFTs (in place,
+// natural order; the caller must __syncthreads() before; ends with a barrier).
 template <typename T, int N, int NB, int LD, int NT, int S>
 __device__ __forceinline__ void smem_fft_pair(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;

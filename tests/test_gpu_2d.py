@@ -212,13 +212,14 @@ def test_every_fft_schedule_gives_the_same_operator(n):
             assert np.abs(q - ref).max() <= 2e-5 * np.abs(ref).max(), sch
 
 
-def test_lane_pair_transform_variant_at_1024():
-    """Tile variant 5 of the first pass at n_x = 1024 (each 32-point register FFT
-    of the x transform spread over a lane pair) applies the same operator as the
-    oracle (FP32, to 2e-5 of the field maximum) and runs the same CG as
-    variant 0 (three load cases, C_eff to 1e-10, and the oracle's to 1e-9)."""
+@pytest.mark.parametrize("n", [(1024, 32), (512, 64)])
+def test_lane_pair_transform_variant(n):
+    """Tile variant 5 of the first pass at n_x = 1024 and 512 (each 32-point
+    register FFT of the x transform's first step spread over a lane pair)
+    applies the same operator as the oracle (FP32, to 2e-5 of the field
+    maximum) and runs the same CG as variant 0 (three load cases, C_eff to
+    1e-10, and the oracle's to 1e-9)."""
     from paper_2105_03297_gb300 import RVE
-    n = (1024, 32)
     E = lognormal(n, 64)
     P = Problem(n, E, 0.3)
     p = np.random.default_rng(65).standard_normal((P.m,) + E.shape).astype(np.float32).astype(np.float64)
