@@ -95,3 +95,33 @@ def test_missing_library_fails_loudly(tmp_path):
             _rve.load(str(tmp_path / "librve.so"))
     finally:
         _rve._lib = saved
+
+
+def _header_constants():
+    """Every RVE_* constant of include/rve.h (enum members and #defines)."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "rve.h")
+    src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"(RVE_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    for name, val in re.findall(r"#define\s+(RVE_[A-Z0-9_]+)\s+(-?\d+)", src):
+        consts[name] = int(val)
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    h = _header_constants()
+    for name in ("RVE_OK", "RVE_ERR_ARG", "RVE_ERR_UNSUPPORTED_SIZE", "RVE_ERR_CUDA", "RVE_ERR_OOM",
+                 "RVE_ERR_NOT_CONVERGED", "RVE_ERR_NONFINITE", "RVE_ERR_TIMEOUT", "RVE_ERR_SCRATCH_LIMIT",
+                 "RVE_FP64", "RVE_MIXED", "RVE_F32", "RVE_F64", "RVE_PTR_HOST", "RVE_PTR_DEVICE"):
+        assert getattr(_rve, name) == h[name], name
+    assert (_rve.RVE.SCHED_PASSES, _rve.RVE.SCHED_VARIANTS) == (h["RVE_SCHED_PASSES"], h["RVE_SCHED_VARIANTS"])
+    assert _rve.RVE.FORMS == {"stress": h["RVE_FORM_STRESS"], "factored": h["RVE_FORM_FACTORED"],
+                              "nodal": h["RVE_FORM_NODAL"]}
+    assert len(_rve.RVE.KINDS) == h["RVE_NKINDS"]
+    assert _rve.RVE.DERIVATIVES == {"fe": h["RVE_DERIV_FE"], "fourier": h["RVE_DERIV_FOURIER"],
+                                    "central": h["RVE_DERIV_CENTRAL"], "forward": h["RVE_DERIV_FORWARD"],
+                                    "lsq": h["RVE_DERIV_LSQ"], "fourier2": h["RVE_DERIV_FOURIER2"]}
