@@ -28,14 +28,15 @@ __host__ __device__ constexpr int kuhn_perm(int t, int i) {
 }
 
 // --------------------------------------------- L2 prefetch of a later tile
-// Passes A and E run grids of (n_y/TY, n_z, L*G) blocks, far more than are
-// resident, and the blocks start in about linear launch order as earlier ones
-// retire.  With a.pf_ahead = D > 0 every block asks the TMA unit to bring the
-// rows of block b + D (b its own linear index) into L2 (bulk prefetches: no
-// data reaches the SM and nothing waits on them), so that DRAM keeps streaming
-// a later tile while this block transforms its own.  Decomposes a linear
-// block index of that grid; false past the end of the grid or for a load case
-// whose CG has stopped.
+// The transform passes run grids of far more blocks than are resident, and
+// the blocks start in about linear launch order as earlier ones retire.  With
+// a.pf_ahead = D > 0 every block asks the TMA unit to bring the input of
+// block b + D (b its own linear index) into L2 (bulk prefetches: no data
+// reaches the SM and nothing waits on them), so that DRAM keeps streaming a
+// later tile while this block transforms its own (passes A and E: tile
+// variants 6 and 4; passes B, C and D: always in FP32; the distances are in
+// prefetch_distance).
+//
 // Block coordinates (x, y, z) of the block a.pf_ahead places after this one in
 // launch order; false past the end of the grid.
 template <typename T>
@@ -54,7 +55,8 @@ template <typename T> __device__ __forceinline__ bool slot_runs(const PassArgs<T
   const CgState* cg = a.cg + l;
   return cg->active && !(a.cgphase && cg->status != ST_RUN);
 }
-// Passes A and E: tile (l, grp, z, y0) of the later block.
+// Passes A and E (grid (n_y/TY, n_z, L*G)): tile (l, grp, z, y0) of the later
+// block; false past the end of the grid or for a load case whose CG has stopped.
 template <typename T>
 __device__ __forceinline__ bool block_ahead(const PassArgs<T>& a, int G, int TY, int& l, int& grp, int& z, int& y0) {
   int bx, bz;
